@@ -1,0 +1,109 @@
+"""Seeded synthetic quark-propagator fields shared by the CUDA path's tests and the oracle.
+
+This module holds only the input recipe (random numbers and their layout), none of the
+correlator arithmetic, so that both sides of a parity test can regenerate exactly the same
+inputs without depending on each other.
+
+Recipe
+------
+A propagator field for flavour ``f`` on an ``L^3 x T`` lattice is a complex array
+``S[set][t][site][i][j]`` of 12x12 spin-colour matrices (row ``i`` = sink, column ``j`` =
+source, ``i = 3*spin + colour``).  Every entry is
+
+    S = exp(-kappa * t) * G            (plain fields)
+    S = exp(-kappa * t) * (B_t + eps * G)   (``noise=eps``: a base matrix shared by all
+                                              sites of a time slice plus relative noise)
+
+with ``G`` complex standard normal, CN(0, 1): real and imaginary parts independent
+N(0, 1/2).  ``G`` is drawn from a counter-based generator so that any single site can be
+regenerated on its own:
+
+* ``stream = mix(mix(mix(seed) ^ set) ^ (flavour << 32 | t))`` with ``mix`` the SplitMix64
+  output function (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+  OOPSLA 2014), ``flavour`` 0 for up and 1 for down;
+* the entry with flat index ``n = site * 144 + 12 * i + j`` takes outputs ``2n + 1`` and
+  ``2n + 2`` of the SplitMix64 sequence started at ``stream``, i.e.
+  ``z_k = mix(stream + k * 0x9e3779b97f4a7c15)``;
+* the two outputs become uniforms ``u1 = ((z1 >> 11) + 1) * 2^-53`` in (0, 1] and
+  ``u2 = (z2 >> 11) * 2^-53`` in [0, 1), and the Box-Muller transform gives
+  ``G = sqrt(-ln u1) * (cos(2 pi u2) + i sin(2 pi u2))``;
+* the shared base ``B_t`` uses ``site = -1`` mapped to ``2^40`` in the counter.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+BASE_SITE = 1 << 40
+N_SC = 12  # spin x colour
+
+
+def _mix(z):
+    """SplitMix64 output function on a uint64 array (wrap-around arithmetic)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_key(seed: int, set_index: int, flavour: int, t: int) -> np.uint64:
+    """Per-(seed, set, flavour, t) starting point of the SplitMix64 sequence."""
+    with np.errstate(over="ignore"):
+        h = _mix(np.uint64(seed) + GOLDEN)
+        h = _mix(h ^ np.uint64(set_index))
+        h = _mix(h ^ np.uint64((flavour << 32) | t))
+    return np.uint64(h)
+
+
+def gaussian_entries(stream: np.uint64, counters: np.ndarray) -> np.ndarray:
+    """CN(0,1) values for the given flat entry counters of one stream."""
+    n = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        k1 = np.uint64(2) * n + np.uint64(1)
+        z1 = _mix(stream + k1 * GOLDEN)
+        z2 = _mix(stream + (k1 + np.uint64(1)) * GOLDEN)
+    u1 = ((z1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0**-53
+    u2 = (z2 >> np.uint64(11)).astype(np.float64) * 2.0**-53
+    r = np.sqrt(-np.log(u1))
+    th = 2.0 * np.pi * u2
+    return r * np.cos(th) + 1j * r * np.sin(th)
+
+
+def site_matrices(seed: int, set_index: int, flavour: int, t: int, sites, kappa: float = 0.5,
+                  noise: float | None = None) -> np.ndarray:
+    """12x12 propagator matrices of the listed sites of one time slice, shape [n, 12, 12]."""
+    sites = np.asarray(sites, dtype=np.int64).reshape(-1)
+    st = stream_key(seed, set_index, flavour, t)
+    e = np.arange(N_SC * N_SC, dtype=np.uint64)
+    cnt = sites.astype(np.uint64)[:, None] * np.uint64(N_SC * N_SC) + e[None, :]
+    g = gaussian_entries(st, cnt).reshape(-1, N_SC, N_SC)
+    if noise is not None:
+        base_cnt = np.uint64(BASE_SITE) * np.uint64(N_SC * N_SC) + e
+        b = gaussian_entries(st, base_cnt).reshape(N_SC, N_SC)
+        g = b[None] + noise * g
+    return np.exp(-kappa * t) * g
+
+
+def propagator_field(seed: int, set_index: int, flavour: int, T: int, V3: int, kappa: float = 0.5,
+                     noise: float | None = None, t_list=None) -> np.ndarray:
+    """Whole field of one set and flavour, shape [T, V3, 12, 12] complex128 (or the listed t)."""
+    ts = range(T) if t_list is None else t_list
+    out = np.empty((len(ts), V3, N_SC, N_SC), dtype=np.complex128)
+    sites = np.arange(V3, dtype=np.int64)
+    for k, t in enumerate(ts):
+        out[k] = site_matrices(seed, set_index, flavour, t, sites, kappa, noise)
+    return out
+
+
+def su3_random(rng: np.random.Generator, n: int) -> np.ndarray:
+    """n Haar-ish random SU(3) matrices (QR of a complex Gaussian, phase-fixed, det 1)."""
+    z = (rng.standard_normal((n, 3, 3)) + 1j * rng.standard_normal((n, 3, 3))) / np.sqrt(2)
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=1, axis2=2)
+    q = q * (d / np.abs(d))[:, None, :]
+    det = np.linalg.det(q)
+    q = q / (det ** (1.0 / 3.0))[:, None, None]
+    return q
