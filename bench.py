@@ -1,0 +1,296 @@
+"""Benchmark: sink-site contractions per second of the 3He correlator at 24^3 x 48.
+
+One step = one evaluation of the correlator C(t) of the 3He_II-s operator (the stand-in
+for the printed 3He_II, which vanishes identically) over every sink site of a 24^3 x 48
+lattice (663552 sink-site contractions), with the e-graph plan in the mixed (double-float)
+arithmetic: staging, minors, contraction and the site sum, all in the library's kernels.
+Inputs (2 x 1.5 GB of complex double propagators) are resident in HBM and larger than L2.
+
+Prints one JSON line (rank 0).  Extra keys: roofline of the dominant kernel, the FP64
+plan on a subset of time slices (same metric) and the mixed-vs-FP64 relative error,
+the oracle timed on the host cores (cpu_baseline), an end-to-end figure through the
+host-buffer entry point, SM clocks sampled during the timed region and the number of
+kernel launches.  ``--impl reference`` times the oracle instead (on a bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sink-site contractions/sec (He-3 II, 24^3x48), FP64 vs mixed, % FLOP peak"
+UNIT = "contractions/s"
+OPERATOR = "he3_II_s"
+L, T = 24, 48
+SEED, KAPPA = 3, 0.5
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 sub-partitions x 32)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak from unit counts and clock: SMs x lanes x 2 flop x clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fields(set_index, t_list=None):
+    import mbc_inputs as mi
+    U = mi.propagator_field(SEED, set_index, 0, T, L ** 3, KAPPA, None, t_list)
+    D = mi.propagator_field(SEED, set_index, 1, T, L ** 3, KAPPA, None, t_list)
+    return U, D
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(n_sites_target=None, seconds=20.0):
+    """The oracle (canonical form, plain C, OpenMP over sites) on a bounded sample of
+    the same workload: sites spread over the time slices."""
+    from oracle import correlator as ocor
+    from oracle import native
+    from oracle import operators as oops
+    import mbc_inputs as mi
+    native.build()
+    plan = ocor.CanonicalPlan(oops.build(OPERATOR))
+    threads = native.max_threads()
+    rng = np.random.default_rng(0)
+    # calibrate on a few sites, then size the sample to ~`seconds` of wall time
+    probe = [(t, int(rng.integers(L ** 3))) for t in rng.choice(T, size=max(threads, 4))]
+
+    def regen(pts):
+        U = np.concatenate([mi.site_matrices(SEED, 0, 0, t, [x], KAPPA) for t, x in pts])
+        D = np.concatenate([mi.site_matrices(SEED, 0, 1, t, [x], KAPPA) for t, x in pts])
+        return U, D
+
+    U, D = regen(probe)
+    t0 = time.perf_counter()
+    plan.site_values(U, D, n_threads=threads)
+    dt = time.perf_counter() - t0
+    n = n_sites_target or max(threads, int(seconds / max(dt / len(probe), 1e-9)))
+    pts = [(int(t), int(rng.integers(L ** 3))) for t in rng.integers(0, T, size=n)]
+    U, D = regen(pts)
+    t0 = time.perf_counter()
+    plan.site_values(U, D, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} random sink sites of {OPERATOR} {L}^3x{T} (canonical merged form, plain C, "
+                      f"OpenMP over sites), {dt:.1f} s"}, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    meta = None
+    for i in range(args.warmup + args.steps):
+        meta, dt = cpu_baseline(seconds=min(20.0, 100.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            steps.append(dt)
+    value = meta["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{OPERATOR} (stand-in for He-3 II) {L}^3x{T}, one source, oracle on a sample"},
+            "cpu_baseline": meta, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mbc", choices=["mbc", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--fp64-slices", type=int, default=4)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2201_04269_gb300 import Context, build
+
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+
+    # weak scaling: every rank evaluates its own propagator set (its own source time)
+    U_h, D_h = fields(rank)
+    n_sites = T * L ** 3
+    U = torch.from_numpy(U_h).cuda()[None]
+    D = torch.from_numpy(D_h).cuda()[None]
+    C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    ctx = Context(local)
+    plan = ctx.plan_operator(OPERATOR, "egraph", "mixed")
+    info = plan.info
+
+    def step():
+        plan.correlator(U, D, C, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches0 = ctx.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = ctx.launches - launches0
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    clocks = clk.summary()
+    C_mixed = C.cpu().numpy()[0].copy()
+
+    # dominant kernel alone: the e-graph kernel plus its two small reduction kernels
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    flops = info["flops_per_site"] * n_sites
+    achieved = flops / (ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(sm_max)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "egraph_kernel<MIXED>",
+                "flops_per_site": info["flops_per_site"], "flop_model": "8 flop per complex multiply-add of the plan",
+                "peak_basis": f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz (derived)"}
+
+    # FP64 plan on a subset of time slices (same metric), and the mixed error against it
+    fp64 = None
+    if args.fp64_slices > 0:
+        ts = list(np.linspace(0, T - 1, args.fp64_slices).round().astype(int))
+        p64 = ctx.plan_operator(OPERATOR, "egraph", "fp64")
+        Us, Ds = U[:, ts].contiguous(), D[:, ts].contiguous()
+        C64 = torch.zeros(1, len(ts), dtype=torch.complex128, device="cuda")
+        p64.correlator(Us, Ds, C64, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p64.correlator(Us, Ds, C64, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        c64 = C64.cpu().numpy()[0]
+        err = float(np.max(np.abs(C_mixed[ts] - c64) / np.abs(c64)))
+        n64 = len(ts) * L ** 3
+        fp64 = {"value": n64 / (ms64 * 1e-3), "unit": UNIT, "time_slices": [int(t) for t in ts],
+                "tflops": p64.info["flops_per_site"] * n64 / (ms64 * 1e-3) / 1e12,
+                "mixed_speedup": (n_sites / (ms * 1e-3)) / (n64 / (ms64 * 1e-3)),
+                "rel_err_mixed_vs_fp64": err}
+        p64.destroy()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    U_pin = torch.from_numpy(U_h[None]).pin_memory()
+    D_pin = torch.from_numpy(D_h[None]).pin_memory()
+    C_pin = torch.zeros(1, T, dtype=torch.complex128).pin_memory()
+    plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * n_sites / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(U_pin.numel() * 16 * 2),
+           "d2h_bytes_per_step": int(C_pin.numel() * 16)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu, _ = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * n_sites / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
+                "config": {"workload": f"{OPERATOR} (stand-in for He-3 II) {L}^3x{T}, one source per GPU, "
+                                       f"P+ traced, e-graph plan, mixed (double-float)",
+                           "sites_per_gpu": n_sites, "l2": "inputs 3.2 GB per GPU, larger than L2",
+                           "canonical_terms": info["canonical_terms"], "index_size": info["index_size"]},
+                "roofline": roofline, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

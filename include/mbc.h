@@ -1,0 +1,224 @@
+/* mbc.h - C ABI of libmbc: multi-baryon two-point correlators on GB300 (sm_103a).
+ *
+ * Computes the correlator of arXiv 2201.04269, Eq. 1,
+ *
+ *     C = sum_{(a, a') in I} W^{a}_{a'} <q(a_1)...q(a_n) qbar(a'_1)...qbar(a'_n)>,
+ *
+ * for quark-only operators with n_u up and n_d down quarks, with every quark at one
+ * sink site x and every antiquark at one source point, summed over the sink sites of
+ * each time slice (zero momentum).  The quark-level Wick contraction is evaluated in
+ * its determinant form (Sec. 1): after the caller has written the slots of every term
+ * in flavour-grouped order (all up slots, then all down slots) and folded the
+ * reordering signs into the weights,
+ *
+ *     C_x(t) = scale * sum_{(a, a') in I} W(a, a') det U_x[a_u, a'_u] det D_x[a_d, a'_d],
+ *
+ * with scale carrying (-1)^{n(n-1)/2} and any normalisation.  Three algorithms:
+ * the direct index-set sweep (MBC_ALGO_DIRECT), factor trees (Sec. 4,
+ * MBC_ALGO_TREE) and a plan extracted from a tensor e-graph (Sec. 5, MBC_ALGO_EGRAPH);
+ * two arithmetics: complex double (MBC_PREC_FP64) and complex FP32 pairs with
+ * compensated products and double accumulation (MBC_PREC_MIXED).
+ *
+ * Conventions for every call:
+ *  - Spin-colour index i = 3 * spin + colour in 0..11.  A propagator field is a device
+ *    array of complex double (interleaved re, im), layout [set][t][site][12][12],
+ *    row = sink index, column = source index; it is owned by the caller.
+ *  - Calls never throw; they return an mbc_status.  Failed calls leave outputs
+ *    unchanged and record a message readable through mbc_last_error(ctx).
+ *  - Device work is enqueued on the caller's stream and is asynchronous; a plan is
+ *    immutable after creation and may be used from several streams at once as long as
+ *    each call has its own output buffers.  No call synchronises the device except
+ *    where stated.
+ */
+#ifndef MBC_H
+#define MBC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mbc_stream;   /* a cudaStream_t; NULL = the legacy default stream */
+
+typedef enum {
+    MBC_OK = 0,
+    MBC_INVALID_ARG = 1,   /* null pointer, negative size, inconsistent offsets, bad enum */
+    MBC_UNSUPPORTED = 2,   /* n_u or n_d outside 0..6, index outside 0..11, algorithm not
+                              available for this kind of plan */
+    MBC_OOM = 3,           /* host or device allocation failed */
+    MBC_CUDA = 4,          /* a CUDA runtime call failed (message names it) */
+    MBC_TIMEOUT = 5,       /* a bounded device wait gave up */
+    MBC_NUMERIC = 6,       /* non-finite input or result */
+    MBC_IO = 7             /* plan file missing, truncated or of another version */
+} mbc_status;
+
+typedef enum { MBC_ALGO_DIRECT = 0, MBC_ALGO_TREE = 1, MBC_ALGO_EGRAPH = 2 } mbc_algo;
+typedef enum { MBC_PREC_FP64 = 0, MBC_PREC_MIXED = 1 } mbc_prec;
+
+typedef struct mbc_ctx mbc_ctx;
+typedef struct mbc_plan mbc_plan;
+
+/* ------------------------------------------------------------------------------------
+ * Context.  mbc_create binds a context to a CUDA device; the context owns its plans'
+ * device memory.  device = -1 makes a host-only context: plans are built and can be
+ * inspected, saved and loaded, but evaluation calls return MBC_UNSUPPORTED (no CUDA
+ * call is made).  mbc_destroy frees everything the context owns (plans included).
+ * ---------------------------------------------------------------------------------- */
+mbc_status mbc_create(mbc_ctx** ctx, int device);
+void mbc_destroy(mbc_ctx* ctx);
+/* Message of the last failed call on this context (never NULL; "" if none).  The
+ * string is owned by the context and valid until its next call. */
+const char* mbc_last_error(const mbc_ctx* ctx);
+/* Library version, e.g. "mbc 1.0". */
+const char* mbc_version(void);
+
+/* ------------------------------------------------------------------------------------
+ * Operator library: the baryon and multi-baryon operators of Sec. 1 and Eq. 2
+ * (proton, neutron, D_I, D_II, 3He_I, 3He_II) expanded into sink terms.
+ *
+ * Each operator is expanded into ordered products of quark fields; each product is
+ * written in flavour-grouped slot order with the sign of that Grassmann reordering
+ * folded into its weight; identical slot tuples are merged.  Weights are returned
+ * unnormalised (Gaussian integers, so merging is exact); *scale receives
+ * (-1)^{n(n-1)/2} |norm|^2 for the correlator of the operator with itself.  Readings
+ * where the paper is silent: Dirac basis with C = gamma_4 gamma_2; the free spin index
+ * (proton, neutron, 3He) is projected with P_+ = (1 + gamma_4)/2 and traced; the
+ * source uses the conjugated sink weights.  MBC_OP_HE3_II_S is a stand-in for 3He_II
+ * (its printed terms 1, 2, 5 with normalisation 2/sqrt(6)), because the printed D_II
+ * and 3He_II vanish identically.
+ *
+ * Call with idx == NULL to query sizes: *n_terms receives the total term count.
+ * Otherwise idx must hold n_terms * (n_u + n_d) bytes, w 2 * n_terms doubles,
+ * offsets n_free + 1 entries (terms of free index j are offsets[j]..offsets[j+1]-1),
+ * proj 2 * n_free * n_free doubles (row-major complex P_jj').
+ * ---------------------------------------------------------------------------------- */
+typedef enum {
+    MBC_OP_PROTON = 0, MBC_OP_NEUTRON = 1, MBC_OP_DINUCLEON_I = 2, MBC_OP_DINUCLEON_II = 3,
+    MBC_OP_HE3_I = 4, MBC_OP_HE3_II = 5, MBC_OP_HE3_II_S = 6
+} mbc_operator;
+
+mbc_status mbc_operator_terms(int op, int* n_u, int* n_d, int* n_free, int64_t* n_terms,
+                              int8_t* idx, double* w, int64_t* offsets, double* proj, double* scale);
+
+/* ------------------------------------------------------------------------------------
+ * Plans.
+ *
+ * mbc_plan_create: a factored weight (Eq. 1 with W factorised over sink and source)
+ *     W(a, a') = sum_{j, j'} P_jj' s_j(a) conj(r_j'(a')),
+ * j, j' in 0..n_free-1.  snk_idx [n_snk][n_u + n_d] int8 slot indices (flavour
+ * grouped), snk_w [n_snk] complex double, snk_off [n_free + 1]; the same for the
+ * source; proj [n_free][n_free] complex double; scale a complex double multiplying C
+ * (pass {(-1)^{n(n-1)/2}, 0} for the plain Wick sign).  All pointers are host memory,
+ * read during the call only.
+ *
+ * The planner (host, once per plan; Sec. 3-5) canonicalises every term (ascending
+ * slot sets per flavour with the sorting sign, repeated indices dropped: the
+ * Index-List pruning), merges multiplicities, builds the linearised factor tree and
+ * runs the minor e-graph, then uploads what the chosen algorithm needs to the device.
+ *
+ * mbc_plan_from_terms: explicit index set, term t = (a_t, a'_t, W_t) with
+ * a = sink[t][n_u + n_d], a' = source[t][n_u + n_d], W [n_terms] complex double.
+ * Supports MBC_ALGO_DIRECT and MBC_ALGO_TREE (MBC_UNSUPPORTED otherwise).
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+    int n_u, n_d, n_free;
+    const int8_t* snk_idx; const double* snk_w; const int64_t* snk_off;
+    const int8_t* src_idx; const double* src_w; const int64_t* src_off;
+    const double* proj;
+    double scale[2];
+} mbc_problem;
+
+mbc_status mbc_plan_create(mbc_ctx* ctx, const mbc_problem* problem, int algo, int prec, mbc_plan** out);
+mbc_status mbc_plan_from_terms(mbc_ctx* ctx, int n_u, int n_d, int64_t n_terms,
+                               const int8_t* sink, const int8_t* source, const double* W,
+                               const double* scale, int algo, int prec, mbc_plan** out);
+void mbc_plan_destroy(mbc_plan* plan);
+
+/* Plan statistics (host values): */
+typedef struct {
+    int n_u, n_d, algo, prec;
+    int64_t index_size;          /* |I|: (sink, source) term pairs of the direct sweep */
+    int64_t canonical_terms;     /* merged canonical (R_u, R_d, C_u, C_d) terms (tree leaves) */
+    int64_t rows_u, rows_d, cols_u, cols_d;   /* distinct ascending slot sets */
+    int64_t minors_u, minors_d;  /* distinct minors the canonical form needs */
+    int64_t tree_nodes;          /* vertices of the linearised factor tree (root included) */
+    int64_t egraph_classes, egraph_nodes;     /* saturated minor e-graph size */
+    double flops_per_site;       /* algorithmic flops of this plan's algorithm, per site */
+    double direct_flops_per_site;/* the direct sweep's flops, per site (for comparison) */
+    int64_t scratch_bytes_per_site; /* device scratch the algorithm uses per in-flight site */
+} mbc_plan_info;
+mbc_status mbc_plan_get_info(const mbc_plan* plan, mbc_plan_info* info);
+
+/* Linearised factor tree of the plan (Sec. 4, Fig. 5): factors[n_nodes] (factors[0]
+ * is the root and is -1; up minor m is m, down minor m is minors_u + m), children
+ * [n_nodes], coefficients [n_leaves] complex double (scale not applied).  Pass NULL
+ * arrays to query n_nodes / n_leaves.  Minor m of flavour f is (rows, cols) given by
+ * mbc_plan_get_minor. */
+mbc_status mbc_plan_get_tree(const mbc_plan* plan, int64_t* n_nodes, int64_t* n_leaves,
+                             int32_t* factors, int32_t* children, double* coefficients);
+mbc_status mbc_plan_get_minor(const mbc_plan* plan, int flavour, int64_t m, int8_t* rows, int8_t* cols);
+
+/* Serialise a plan (problem, canonical lists, tree, e-graph plan) to a versioned file,
+ * and load it back (the planner is not re-run). */
+mbc_status mbc_plan_save(const mbc_plan* plan, const char* path);
+mbc_status mbc_plan_load(mbc_ctx* ctx, const char* path, mbc_plan** out);
+
+/* ------------------------------------------------------------------------------------
+ * Evaluation.
+ *
+ * mbc_correlator: C[s][t] = scale * sum_{x < V3} C_x(s, t) for every set s < n_sets and
+ * time slice t < T.  U, D: device pointers, complex double [n_sets][T][V3][12][12]
+ * (caller-owned).  C: device pointer, complex double [n_sets][T] (written, not
+ * accumulated).  site_out: optional device pointer, complex double [n_sets][T][V3]
+ * receiving scale * C_x per site, or NULL.  The site sum is taken in double with
+ * compensated (TwoSum) accumulation in a fixed order, so results are bit-reproducible
+ * for a given plan, sizes and device.  Temporary device memory is taken from the
+ * context's pool (grown on demand with cudaMalloc outside any stream capture).
+ * ---------------------------------------------------------------------------------- */
+mbc_status mbc_correlator(mbc_plan* plan, const void* U, const void* D, int n_sets, int T, int64_t V3,
+                          void* C, void* site_out, mbc_stream stream);
+
+/* End to end from host memory: copies U, D (host, pinned or pageable, same layout) to
+ * the context's device buffers, evaluates, copies C back to host memory C_host, on
+ * the given stream, and synchronises that stream before returning. */
+mbc_status mbc_correlator_host(mbc_plan* plan, const void* U_host, const void* D_host, int n_sets, int T,
+                               int64_t V3, void* C_host, mbc_stream stream);
+
+/* Batched evaluation: several (plan, fields, output) items in one persistent launch per
+ * kernel family, load-balanced over (item, set, t, site block) work units by an atomic
+ * counter (no inter-block waiting).  Items must use plans of this context; an item's
+ * algorithm must be MBC_ALGO_EGRAPH (the batched scheduler runs the e-graph kernels).
+ * Capturable in a CUDA graph once mbc_batch_reserve has sized the pool for the items. */
+typedef struct {
+    mbc_plan* plan;
+    const void* U;
+    const void* D;
+    int n_sets, T;
+    int64_t V3;
+    void* C;                    /* device complex double [n_sets][T] */
+} mbc_work;
+mbc_status mbc_batch_reserve(mbc_ctx* ctx, const mbc_work* items, int n_items);
+mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_stream stream);
+
+/* ------------------------------------------------------------------------------------
+ * Launch schedule and autotuning.  A schedule is (threads per block, blocks per SM,
+ * sites per work unit); mbc_autotune times the candidate schedules of the plan's
+ * kernel on the given fields (a few sites per candidate), keeps the fastest in the
+ * plan and in the context's cache keyed by (plan signature, device), and reports it.
+ * Synchronises the stream.
+ * ---------------------------------------------------------------------------------- */
+typedef struct { int threads; int blocks_per_sm; int sites_per_unit; } mbc_schedule;
+mbc_status mbc_autotune(mbc_plan* plan, const void* U, const void* D, int64_t n_sites, mbc_stream stream,
+                        mbc_schedule* best);
+mbc_status mbc_set_schedule(mbc_plan* plan, const mbc_schedule* s);
+mbc_status mbc_get_schedule(const mbc_plan* plan, mbc_schedule* s);
+
+/* Number of device kernel launches made by this context since it was created (every
+ * launch of every mbc call counts once). */
+int64_t mbc_launch_count(const mbc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBC_H */

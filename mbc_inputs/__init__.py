@@ -31,6 +31,9 @@ regenerated on its own:
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -90,11 +93,21 @@ def site_matrices(seed: int, set_index: int, flavour: int, t: int, sites, kappa:
 def propagator_field(seed: int, set_index: int, flavour: int, T: int, V3: int, kappa: float = 0.5,
                      noise: float | None = None, t_list=None) -> np.ndarray:
     """Whole field of one set and flavour, shape [T, V3, 12, 12] complex128 (or the listed t)."""
-    ts = range(T) if t_list is None else t_list
+    ts = list(range(T) if t_list is None else t_list)
     out = np.empty((len(ts), V3, N_SC, N_SC), dtype=np.complex128)
     sites = np.arange(V3, dtype=np.int64)
-    for k, t in enumerate(ts):
-        out[k] = site_matrices(seed, set_index, flavour, t, sites, kappa, noise)
+
+    def fill(k):
+        out[k] = site_matrices(seed, set_index, flavour, ts[k], sites, kappa, noise)
+
+    # numpy releases the GIL inside its array loops, so time slices fill in parallel
+    workers = max(1, min(len(ts), os.cpu_count() or 1, 32))
+    if workers > 1 and V3 * len(ts) > 4096:
+        with ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(fill, range(len(ts))))
+    else:
+        for k in range(len(ts)):
+            fill(k)
     return out
 
 
@@ -107,3 +120,27 @@ def su3_random(rng: np.random.Generator, n: int) -> np.ndarray:
     det = np.linalg.det(q)
     q = q / (det ** (1.0 / 3.0))[:, None, None]
     return q
+
+
+# Synthetic stand-ins for the paper's workloads (lattice L^3 x T, one propagator set per
+# source time or configuration); the paper's gauge ensembles are not available.
+WORKLOADS = {
+    "proton_4x8": dict(ops=("proton",), L=4, T=8, seed=1, kappa=0.5, noise=None, sets=1),
+    "dinucleon_16x32": dict(ops=("dinucleon_I", "dinucleon_II"), L=16, T=32, seed=2, kappa=0.5, noise=None, sets=1),
+    "he3_24x48": dict(ops=("he3_I", "he3_II", "he3_II_s"), L=24, T=48, seed=3, kappa=0.5, noise=None, sets=1),
+    "batched_64": dict(ops=("proton", "dinucleon_I", "dinucleon_II", "he3_I", "he3_II"), L=(16, 24), T=(32, 48),
+                       seed=100, kappa=0.5, noise=None, sets=64),
+    "he3_32x64_8src": dict(ops=("he3_II", "he3_II_s"), L=32, T=64, seed=5, kappa=0.3, noise=1e-3, sets=8),
+}
+
+
+def workload_fields(name: str, set_index: int = 0, t_list=None, L=None, T=None):
+    """(U, D) numpy fields [T', V3, 12, 12] of one set of a named workload."""
+    w = WORKLOADS[name]
+    L = L or (w["L"] if isinstance(w["L"], int) else w["L"][0])
+    T = T or (w["T"] if isinstance(w["T"], int) else w["T"][0])
+    V3 = L ** 3
+    seed = w["seed"] + (set_index if name == "batched_64" else 0)
+    U = propagator_field(seed, set_index, 0, T, V3, w["kappa"], w["noise"], t_list)
+    D = propagator_field(seed, set_index, 1, T, V3, w["kappa"], w["noise"], t_list)
+    return U, D

@@ -1,0 +1,688 @@
+// api.cu - the C ABI of libmbc (see include/mbc.h): contexts, plans, device upload,
+// evaluation, batching, autotuning and plan files.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mbc.h"
+#include "device.cuh"
+#include "plan.hpp"
+
+using namespace mbc;
+
+namespace {
+
+// A growable device buffer of the context's pool.
+struct Buf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct mbc_ctx {
+    int device = 0;
+    std::string err;
+    int64_t launches = 0;
+    int sms = 0;
+    Buf partials, site_tmp, scratch, exps, counter, hU, hD, hC;
+    std::vector<mbc_plan*> plans;
+    std::map<std::string, mbc_schedule> tune_cache;
+    // batched launches
+    Buf batch_items, batch_parts;
+};
+
+struct mbc_plan {
+    mbc_ctx* ctx = nullptr;
+    HostPlan hp;
+    void* dev = nullptr;          // one device allocation holding every plan array
+    size_t dev_bytes = 0;
+    DirectDev dd{};
+    TreeDev td{};
+    EgraphDev ed{};
+    mbc_schedule sched{256, 2, 1};
+    std::string signature;
+};
+
+namespace {
+
+mbc_status fail(mbc_ctx* c, mbc_status s, const std::string& m) {
+    if (c) c->err = m;
+    return s;
+}
+
+mbc_status cuda_fail(mbc_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, MBC_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Grow a pool buffer (never during a stream capture).
+mbc_status ensure(mbc_ctx* c, Buf& b, size_t bytes, cudaStream_t s) {
+    if (b.n >= bytes) return MBC_OK;
+    if (capturing(s))
+        return fail(c, MBC_OOM, "device pool too small while a stream capture is active: run the call once "
+                                "outside the capture (or mbc_batch_reserve) first");
+    if (b.p) {
+        cudaStreamSynchronize(s);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.n = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) return fail(c, MBC_OOM, std::string("cudaMalloc of pool buffer failed: ") + cudaGetErrorString(e));
+    b.n = want;
+    return MBC_OK;
+}
+
+// ---------------------------------------------------------------- device upload
+struct Blob {
+    std::vector<unsigned char> host;
+    std::vector<std::pair<size_t, void**>> fixups;
+    template <class T> size_t add(const T* p, size_t n) {
+        size_t off = (host.size() + 255) / 256 * 256;
+        host.resize(off + n * sizeof(T));
+        if (n) std::memcpy(host.data() + off, p, n * sizeof(T));
+        return off;
+    }
+    template <class T> size_t add(const std::vector<T>& v) { return add(v.data(), v.size()); }
+};
+
+template <class T> const T* at(void* base, size_t off) { return reinterpret_cast<const T*>(static_cast<unsigned char*>(base) + off); }
+
+std::vector<cd> to_cd(const std::vector<cplx>& v) {
+    std::vector<cd> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = cd_make(v[i].real(), v[i].imag());
+    return o;
+}
+
+void minor_dev_offsets(const MinorPlan& m, int upto, int* size, int* off) {
+    int acc = 0;
+    for (int k = 0; k < 7; ++k) {
+        size[k] = (k == 0) ? 1 : (k <= m.n ? (int)m.level_rows[k].size() : 0);
+        off[k] = acc;
+        if (k <= upto) acc += size[k];
+    }
+}
+
+mbc_status upload(mbc_plan* P) {
+    HostPlan& h = P->hp;
+    Blob b;
+    // direct
+    std::vector<int64_t> blk_start(1, 0), blk_nr;
+    std::vector<cd> blk_p = to_cd(h.direct.blk_p);
+    for (size_t i = 0; i < h.direct.blk_s0.size(); ++i) {
+        int64_t ns = h.direct.blk_s1[i] - h.direct.blk_s0[i], nr = h.direct.blk_r1[i] - h.direct.blk_r0[i];
+        blk_start.push_back(blk_start.back() + ns * nr);
+        blk_nr.push_back(nr);
+    }
+    blk_start.push_back(INT64_MAX);   // sentinel: the block scan never runs past the end
+    size_t o_bs = b.add(blk_start), o_s0 = b.add(h.direct.blk_s0), o_r0 = b.add(h.direct.blk_r0), o_nr = b.add(blk_nr);
+    size_t o_bp = b.add(blk_p);
+    size_t o_si = b.add(h.snk_idx), o_sw = b.add(to_cd(h.snk_w)), o_ri = b.add(h.src_idx), o_rw = b.add(to_cd(h.src_w));
+    size_t o_es = b.add(h.ex_snk), o_er = b.add(h.ex_src), o_ew = b.add(to_cd(h.ex_w));
+    // tree
+    std::vector<int8_t> mr[2], mc[2];
+    int nf[2] = {h.n_u, h.n_d};
+    for (int f = 0; f < 2; ++f)
+        for (size_t m = 0; m < h.tree.minor_rows[f].size(); ++m) {
+            int8_t r[12], c[12];
+            mask_list(h.tree.minor_rows[f][m], r);
+            mask_list(h.tree.minor_cols[f][m], c);
+            for (int i = 0; i < nf[f]; ++i) { mr[f].push_back(r[i]); mc[f].push_back(c[i]); }
+        }
+    size_t o_mr0 = b.add(mr[0]), o_mc0 = b.add(mc[0]), o_mr1 = b.add(mr[1]), o_mc1 = b.add(mc[1]);
+    size_t o_tf = b.add(h.tree.factors), o_tc = b.add(h.tree.children), o_tco = b.add(to_cd(h.tree.coefficients));
+    size_t o_cn = b.add(h.tree.chunk_node), o_cl = b.add(h.tree.chunk_leaf), o_cc = b.add(h.tree.chunk_count);
+    // e-graph
+    EgraphPlan& e = h.eg;
+    struct MinorOffs { size_t child[7], row[7], lev, col, sign, leaf; } mo[2];
+    const MinorPlan* mps[2] = {&e.A, &e.B};
+    for (int w = 0; w < 2; ++w) {
+        const MinorPlan& m = *mps[w];
+        for (int k = 0; k < 7; ++k) { mo[w].child[k] = b.add(m.child[k]); mo[w].row[k] = b.add(m.row[k]); }
+        std::vector<uint8_t> lev, col;
+        std::vector<int8_t> sg;
+        std::vector<int32_t> leaf;
+        for (auto& nd : m.nodes) { lev.push_back(nd.level); col.push_back(nd.col); sg.push_back(nd.sign); leaf.push_back(nd.leaf); }
+        mo[w].lev = b.add(lev); mo[w].col = b.add(col); mo[w].sign = b.add(sg); mo[w].leaf = b.add(leaf);
+    }
+    size_t o_cnodes = b.add(e.cache_nodes), o_cslot = b.add(e.cache_slot_of_node), o_bslot = b.add(e.bcol_slot);
+    size_t o_bpc = b.add(e.bcol_path_col), o_bps = b.add(e.bcol_path_sign);
+    size_t o_goff = b.add(e.g_off), o_gj = b.add(e.g_j), o_ga = b.add(e.g_a), o_gw = b.add(to_cd(e.g_w));
+    size_t o_poff = b.add(e.pair_off), o_pb = b.add(e.pair_b), o_pc = b.add(to_cd(e.pair_coef));
+
+    void* dev = nullptr;
+    cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
+    if (err != cudaSuccess) return fail(P->ctx, MBC_OOM, std::string("cudaMalloc of plan arrays failed: ") + cudaGetErrorString(err));
+    if (!b.host.empty()) {
+        err = cudaMemcpy(dev, b.host.data(), b.host.size(), cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) { cudaFree(dev); return cuda_fail(P->ctx, err, "cudaMemcpy of plan arrays"); }
+    }
+    P->dev = dev;
+    P->dev_bytes = b.host.size();
+
+    DirectDev& dd = P->dd;
+    dd.n_u = h.n_u; dd.n_d = h.n_d; dd.explicit_terms = h.explicit_terms;
+    dd.n_blocks = (int)h.direct.blk_s0.size();
+    dd.blk_start = at<int64_t>(dev, o_bs); dd.blk_s0 = at<int64_t>(dev, o_s0); dd.blk_r0 = at<int64_t>(dev, o_r0);
+    dd.blk_nr = at<int64_t>(dev, o_nr); dd.blk_p = at<cd>(dev, o_bp);
+    dd.snk_idx = at<int8_t>(dev, o_si); dd.snk_w = at<cd>(dev, o_sw); dd.src_idx = at<int8_t>(dev, o_ri); dd.src_w = at<cd>(dev, o_rw);
+    dd.ex_snk = at<int8_t>(dev, o_es); dd.ex_src = at<int8_t>(dev, o_er); dd.ex_w = at<cd>(dev, o_ew);
+    dd.index_size = h.direct.index_size;
+
+    TreeDev& td = P->td;
+    td.n_u = h.n_u; td.n_d = h.n_d;
+    td.n_minors[0] = (int64_t)h.tree.minor_rows[0].size(); td.n_minors[1] = (int64_t)h.tree.minor_rows[1].size();
+    td.minor_rows[0] = at<int8_t>(dev, o_mr0); td.minor_cols[0] = at<int8_t>(dev, o_mc0);
+    td.minor_rows[1] = at<int8_t>(dev, o_mr1); td.minor_cols[1] = at<int8_t>(dev, o_mc1);
+    td.n_nodes = (int64_t)h.tree.factors.size();
+    td.factors = at<int32_t>(dev, o_tf); td.children = at<int32_t>(dev, o_tc); td.coefficients = at<cd>(dev, o_tco);
+    td.n_chunks = (int)h.tree.chunk_node.size();
+    td.chunk_node = at<int64_t>(dev, o_cn); td.chunk_leaf = at<int64_t>(dev, o_cl); td.chunk_count = at<int32_t>(dev, o_cc);
+
+    EgraphDev& ed = P->ed;
+    ed.flav_a = e.flav_a; ed.n_j = e.n_j;
+    MinorDev* md[2] = {&ed.A, &ed.B};
+    int L = e.cache_level;
+    for (int w = 0; w < 2; ++w) {
+        const MinorPlan& m = *mps[w];
+        MinorDev& x = *md[w];
+        x.n = m.n;
+        minor_dev_offsets(m, w == 0 ? m.n : 6, x.size, x.off);
+        for (int k = 0; k < 7; ++k) { x.child[k] = at<uint16_t>(dev, mo[w].child[k]); x.row[k] = at<uint8_t>(dev, mo[w].row[k]); }
+        x.n_nodes = (int)m.nodes.size();
+        x.node_level = at<uint8_t>(dev, mo[w].lev); x.node_col = at<uint8_t>(dev, mo[w].col);
+        x.node_sign = at<int8_t>(dev, mo[w].sign); x.node_leaf = at<int32_t>(dev, mo[w].leaf);
+    }
+    ed.cache_level = L;
+    ed.n_cache_nodes = (int)e.cache_nodes.size();
+    ed.n_cache_slots = e.n_cache_slots;
+    ed.cache_nodes = at<int32_t>(dev, o_cnodes); ed.cache_slot = at<int32_t>(dev, o_cslot); ed.bcol_slot = at<int32_t>(dev, o_bslot);
+    ed.bcol_path_col = at<uint8_t>(dev, o_bpc); ed.bcol_path_sign = at<int8_t>(dev, o_bps);
+    ed.n_rows_b = e.B.n ? (int)e.B.level_rows[e.B.n].size() : 1;
+    ed.g_off = at<int32_t>(dev, o_goff); ed.g_j = at<int32_t>(dev, o_gj); ed.g_a = at<int32_t>(dev, o_ga); ed.g_w = at<cd>(dev, o_gw);
+    ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_coef = at<cd>(dev, o_pc);
+    ed.stack_a = ed.A.off[ed.A.n] + ed.A.size[ed.A.n];
+    ed.stack_b = e.B.n ? ed.B.off[L] : 0;
+    ed.path_b = 0;
+    for (int k = L + 1; k <= e.B.n; ++k) ed.path_b += ed.B.size[k];
+    int max_pairs = 1;
+    for (size_t i = 0; i + 1 < e.pair_off.size(); ++i) max_pairs = std::max(max_pairs, e.pair_off[i + 1] - e.pair_off[i]);
+    ed.n_batch = std::min(max_pairs, 8);
+    auto smem_values = [&](int nbatch) {
+        int fL = e.B.n ? ed.B.size[L] : 1;
+        return 288 + ed.stack_a + ed.stack_b + ed.n_cache_slots * fL + nbatch * ed.path_b + ed.n_j * ed.n_rows_b;
+    };
+    while (ed.n_batch > 1 && smem_values(ed.n_batch) * 16 > 110 * 1024) --ed.n_batch;
+    ed.smem_values = smem_values(ed.n_batch);
+    return MBC_OK;
+}
+
+std::string signature(const HostPlan& h) {
+    // identifies the plan's kernel workload for the autotune cache
+    char buf[256];
+    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%lld/%lld/%zu/%zu", h.n_u, h.n_d, h.algo, h.prec, (long long)h.direct.index_size,
+             (long long)h.terms.size(), h.eg.A.nodes.size(), h.eg.pair_b.size());
+    return buf;
+}
+
+mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
+    HostPlan& h = P->hp;
+    if (h.algo == MBC_ALGO_EGRAPH) {
+        if (h.explicit_terms) { delete P; return fail(ctx, MBC_UNSUPPORTED, "MBC_ALGO_EGRAPH needs a factored problem (mbc_plan_create)"); }
+        if (h.eg.n_j > 64) { delete P; return fail(ctx, MBC_UNSUPPORTED, "e-graph kernels support at most 64 free indices in use"); }
+    }
+    if (h.algo == MBC_ALGO_TREE) {
+        for (size_t i = 1; i < h.tree.factors.size();) {   // the walk expects level 1 -> leaves
+            int32_t nch = h.tree.children[i];
+            for (int32_t k = 1; k <= nch; ++k)
+                if (h.tree.children[i + k] != 0) { delete P; return fail(ctx, MBC_UNSUPPORTED, "factor tree deeper than two levels"); }
+            i += 1 + nch;
+        }
+    }
+    if (ctx->device < 0) {                   // host-only context: keep the host plan only
+        P->signature = signature(h);
+        ctx->plans.push_back(P);
+        *out = P;
+        ctx->err.clear();
+        return MBC_OK;
+    }
+    mbc_status st = upload(P);
+    if (st != MBC_OK) { delete P; return st; }
+    if (h.algo == MBC_ALGO_EGRAPH && P->ed.smem_values * 16 > 200 * 1024) {
+        cudaFree(P->dev);
+        delete P;
+        return fail(ctx, MBC_UNSUPPORTED, "e-graph plan needs more shared memory than a block has");
+    }
+    P->signature = signature(h);
+    auto it = ctx->tune_cache.find(P->signature);
+    if (it != ctx->tune_cache.end()) P->sched = it->second;
+    else if (h.algo == MBC_ALGO_EGRAPH) P->sched.blocks_per_sm = std::max(1, std::min(4, (int)(200 * 1024 / (P->ed.smem_values * 16 + 1024))));
+    ctx->plans.push_back(P);
+    *out = P;
+    ctx->err.clear();
+    return MBC_OK;
+}
+
+int64_t direct_chunk(const mbc_plan* P) { return std::max<int64_t>(1, (int64_t)P->sched.sites_per_unit * 65536); }
+
+mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int64_t V3, void* C, void* site_out,
+               cudaStream_t s) {
+    mbc_ctx* c = P->ctx;
+    if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
+    HostPlan& h = P->hp;
+    Geometry g{n_sets, T, V3};
+    const int64_t n_sites = g.n_sites();
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const cd scale = cd_make(h.scale.real(), h.scale.imag());
+    // plans with an empty canonical term set have C = 0 identically (tree, e-graph)
+    const bool empty = (h.algo != MBC_ALGO_DIRECT && h.terms.empty()) || (h.algo == MBC_ALGO_DIRECT && h.direct.index_size == 0);
+    if (empty || n_sites == 0) {
+        if (n_sets * T > 0) {
+            e = cudaMemsetAsync(C, 0, sizeof(double2) * (size_t)n_sets * T, s);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+        }
+        if (site_out && n_sites) {
+            e = cudaMemsetAsync(site_out, 0, sizeof(double2) * (size_t)n_sites, s);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+        }
+        return MBC_OK;
+    }
+    int n_chunks = 1;
+    int64_t chunk = 0;
+    if (h.algo == MBC_ALGO_DIRECT) {
+        chunk = direct_chunk(P);
+        n_chunks = (int)((h.direct.index_size + chunk - 1) / chunk);
+    } else if (h.algo == MBC_ALGO_TREE) {
+        n_chunks = P->td.n_chunks;
+    }
+    mbc_status st = ensure(c, c->partials, sizeof(d4) * (size_t)n_sites * n_chunks, s);
+    if (st == MBC_OK) st = ensure(c, c->site_tmp, sizeof(d4) * (size_t)n_sites, s);
+    if (st == MBC_OK) st = ensure(c, c->counter, 256, s);
+    if (st != MBC_OK) return st;
+    Partials parts{(d4*)c->partials.p, n_chunks};
+    const double* u = (const double*)U;
+    const double* d = (const double*)D;
+    if (h.algo == MBC_ALGO_DIRECT) {
+        e = launch_direct(P->dd, h.prec, u, d, g, chunk, parts, P->sched.threads, s, &c->launches);
+    } else if (h.algo == MBC_ALGO_TREE) {
+        const int64_t per_site = (int64_t)(P->td.n_minors[0] + P->td.n_minors[1]) * 16;
+        int64_t wave = std::max<int64_t>(32, (int64_t)(2048LL << 20) / std::max<int64_t>(per_site, 1)) / 32 * 32;
+        wave = std::min<int64_t>(wave, (n_sites + 31) / 32 * 32);
+        st = ensure(c, c->scratch, (size_t)per_site * wave, s);
+        if (st == MBC_OK) st = ensure(c, c->exps, sizeof(int) * 2 * (size_t)wave, s);
+        if (st != MBC_OK) return st;
+        e = launch_tree(P->td, h.prec, u, d, g, c->scratch.p, wave, (int*)c->exps.p, parts, P->sched.threads, s, &c->launches);
+    } else {
+        e = launch_egraph(P->ed, h.prec, u, d, g, parts, P->sched.threads, P->sched.blocks_per_sm,
+                          (unsigned int*)c->counter.p, s, &c->launches);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    e = launch_reduce(parts, g, scale, (double2*)C, (double2*)site_out, (d4*)c->site_tmp.p, s, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reduction launch");
+    return MBC_OK;
+}
+
+bool bad_ptr(const void* p) { return p == nullptr; }
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* mbc_version(void) { return "mbc 1.0"; }
+
+mbc_status mbc_create(mbc_ctx** ctx, int device) {
+    if (!ctx) return MBC_INVALID_ARG;
+    *ctx = nullptr;
+    if (device == -1) {                      // host-only: planning and plan files, no evaluation
+        mbc_ctx* c = new (std::nothrow) mbc_ctx();
+        if (!c) return MBC_OOM;
+        c->device = -1;
+        *ctx = c;
+        return MBC_OK;
+    }
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) return MBC_CUDA;
+    if (device < 0 || device >= n) return MBC_INVALID_ARG;
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return MBC_CUDA;
+    mbc_ctx* c = new (std::nothrow) mbc_ctx();
+    if (!c) return MBC_OOM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    *ctx = c;
+    return MBC_OK;
+}
+
+void mbc_destroy(mbc_ctx* c) {
+    if (!c) return;
+    if (c->device < 0) {
+        for (mbc_plan* p : c->plans) delete p;
+        delete c;
+        return;
+    }
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (mbc_plan* p : c->plans) { if (p->dev) cudaFree(p->dev); delete p; }
+    Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
+                   &c->batch_items, &c->batch_parts};
+    for (Buf* b : bufs) if (b->p) cudaFree(b->p);
+    delete c;
+}
+
+const char* mbc_last_error(const mbc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t mbc_launch_count(const mbc_ctx* c) { return c ? c->launches : 0; }
+
+mbc_status mbc_operator_terms(int op, int* n_u, int* n_d, int* n_free, int64_t* n_terms, int8_t* idx, double* w,
+                              int64_t* offsets, double* proj, double* scale) {
+    if (!n_u || !n_d || !n_free || !n_terms) return MBC_INVALID_ARG;
+    int nu, nd, nf;
+    std::vector<int8_t> vi;
+    std::vector<cplx> vw, vp;
+    std::vector<int64_t> vo;
+    double sc;
+    std::string err = operator_terms(op, nu, nd, nf, vi, vw, vo, vp, sc);
+    if (!err.empty()) return MBC_INVALID_ARG;
+    *n_u = nu; *n_d = nd; *n_free = nf; *n_terms = (int64_t)vw.size();
+    if (!idx) return MBC_OK;
+    if (!w || !offsets || !proj) return MBC_INVALID_ARG;
+    std::memcpy(idx, vi.data(), vi.size());
+    for (size_t i = 0; i < vw.size(); ++i) { w[2 * i] = vw[i].real(); w[2 * i + 1] = vw[i].imag(); }
+    std::memcpy(offsets, vo.data(), vo.size() * sizeof(int64_t));
+    for (size_t i = 0; i < vp.size(); ++i) { proj[2 * i] = vp[i].real(); proj[2 * i + 1] = vp[i].imag(); }
+    if (scale) *scale = sc;
+    return MBC_OK;
+}
+
+mbc_status mbc_plan_create(mbc_ctx* ctx, const mbc_problem* pr, int algo, int prec, mbc_plan** out) {
+    if (!ctx) return MBC_INVALID_ARG;
+    if (!pr || !out) return fail(ctx, MBC_INVALID_ARG, "null problem or output pointer");
+    if (algo < 0 || algo > 2 || prec < 0 || prec > 1) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
+    if (pr->n_u < 0 || pr->n_d < 0 || pr->n_u > 6 || pr->n_d > 6 || pr->n_u + pr->n_d == 0)
+        return fail(ctx, MBC_UNSUPPORTED, "n_u, n_d must be in 0..6 (not both 0)");
+    if (pr->n_free < 1 || pr->n_free > 64) return fail(ctx, MBC_INVALID_ARG, "n_free must be in 1..64");
+    if (bad_ptr(pr->snk_off) || bad_ptr(pr->src_off) || bad_ptr(pr->proj)) return fail(ctx, MBC_INVALID_ARG, "null offsets or projector");
+    const int nf = pr->n_free, nq = pr->n_u + pr->n_d;
+    if (pr->snk_off[0] != 0 || pr->src_off[0] != 0) return fail(ctx, MBC_INVALID_ARG, "offsets must start at 0");
+    for (int j = 0; j < nf; ++j)
+        if (pr->snk_off[j + 1] < pr->snk_off[j] || pr->src_off[j + 1] < pr->src_off[j])
+            return fail(ctx, MBC_INVALID_ARG, "offsets must be non-decreasing");
+    const int64_t ns = pr->snk_off[nf], nr = pr->src_off[nf];
+    if ((ns && (bad_ptr(pr->snk_idx) || bad_ptr(pr->snk_w))) || (nr && (bad_ptr(pr->src_idx) || bad_ptr(pr->src_w))))
+        return fail(ctx, MBC_INVALID_ARG, "null term arrays");
+    mbc_plan* P = new (std::nothrow) mbc_plan();
+    if (!P) return fail(ctx, MBC_OOM, "host allocation");
+    P->ctx = ctx;
+    HostPlan& h = P->hp;
+    h.n_u = pr->n_u; h.n_d = pr->n_d; h.n_free = nf; h.algo = algo; h.prec = prec;
+    h.scale = cplx(pr->scale[0], pr->scale[1]);
+    try {
+        h.snk_idx.assign(pr->snk_idx, pr->snk_idx + ns * nq);
+        h.src_idx.assign(pr->src_idx, pr->src_idx + nr * nq);
+        h.snk_w.resize(ns); h.src_w.resize(nr);
+        for (int64_t i = 0; i < ns; ++i) h.snk_w[i] = cplx(pr->snk_w[2 * i], pr->snk_w[2 * i + 1]);
+        for (int64_t i = 0; i < nr; ++i) h.src_w[i] = cplx(pr->src_w[2 * i], pr->src_w[2 * i + 1]);
+        h.snk_off.assign(pr->snk_off, pr->snk_off + nf + 1);
+        h.src_off.assign(pr->src_off, pr->src_off + nf + 1);
+        h.proj.resize((size_t)nf * nf);
+        for (size_t i = 0; i < h.proj.size(); ++i) h.proj[i] = cplx(pr->proj[2 * i], pr->proj[2 * i + 1]);
+        for (auto& x : h.snk_w) if (!std::isfinite(x.real()) || !std::isfinite(x.imag())) { delete P; return fail(ctx, MBC_NUMERIC, "non-finite sink weight"); }
+        for (auto& x : h.src_w) if (!std::isfinite(x.real()) || !std::isfinite(x.imag())) { delete P; return fail(ctx, MBC_NUMERIC, "non-finite source weight"); }
+        std::string err = plan_factored(h);
+        if (!err.empty()) { delete P; return fail(ctx, MBC_UNSUPPORTED, err); }
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return fail(ctx, MBC_OOM, "host allocation during planning");
+    }
+    return finish_plan(ctx, P, out);
+}
+
+mbc_status mbc_plan_from_terms(mbc_ctx* ctx, int n_u, int n_d, int64_t n_terms, const int8_t* sink, const int8_t* source,
+                               const double* W, const double* scale, int algo, int prec, mbc_plan** out) {
+    if (!ctx) return MBC_INVALID_ARG;
+    if (!out || n_terms < 0 || (n_terms && (!sink || !source || !W))) return fail(ctx, MBC_INVALID_ARG, "bad term arrays");
+    if (algo < 0 || algo > 2 || prec < 0 || prec > 1) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
+    if (algo == MBC_ALGO_EGRAPH) return fail(ctx, MBC_UNSUPPORTED, "MBC_ALGO_EGRAPH needs a factored problem (mbc_plan_create)");
+    if (n_u < 0 || n_d < 0 || n_u > 6 || n_d > 6 || n_u + n_d == 0) return fail(ctx, MBC_UNSUPPORTED, "n_u, n_d must be in 0..6");
+    mbc_plan* P = new (std::nothrow) mbc_plan();
+    if (!P) return fail(ctx, MBC_OOM, "host allocation");
+    P->ctx = ctx;
+    HostPlan& h = P->hp;
+    h.n_u = n_u; h.n_d = n_d; h.n_free = 1; h.algo = algo; h.prec = prec;
+    h.scale = scale ? cplx(scale[0], scale[1]) : cplx(1.0, 0.0);
+    const int nq = n_u + n_d;
+    try {
+        h.ex_snk.assign(sink, sink + n_terms * nq);
+        h.ex_src.assign(source, source + n_terms * nq);
+        h.ex_w.resize(n_terms);
+        for (int64_t i = 0; i < n_terms; ++i) h.ex_w[i] = cplx(W[2 * i], W[2 * i + 1]);
+        std::string err = plan_explicit(h);
+        if (!err.empty()) { delete P; return fail(ctx, MBC_UNSUPPORTED, err); }
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return fail(ctx, MBC_OOM, "host allocation during planning");
+    }
+    return finish_plan(ctx, P, out);
+}
+
+void mbc_plan_destroy(mbc_plan* P) {
+    if (!P) return;
+    mbc_ctx* c = P->ctx;
+    if (c) {
+        if (c->device >= 0) {
+            cudaSetDevice(c->device);
+            cudaDeviceSynchronize();
+        }
+        c->plans.erase(std::remove(c->plans.begin(), c->plans.end(), P), c->plans.end());
+    }
+    if (P->dev) cudaFree(P->dev);
+    delete P;
+}
+
+mbc_status mbc_plan_get_info(const mbc_plan* P, mbc_plan_info* info) {
+    if (!P || !info) return MBC_INVALID_ARG;
+    const HostPlan& h = P->hp;
+    std::memset(info, 0, sizeof *info);
+    info->n_u = h.n_u; info->n_d = h.n_d; info->algo = h.algo; info->prec = h.prec;
+    info->index_size = h.direct.index_size;
+    info->canonical_terms = (int64_t)h.terms.size();
+    info->rows_u = (int64_t)h.rows[0].size(); info->rows_d = (int64_t)h.rows[1].size();
+    info->cols_u = (int64_t)h.cols[0].size(); info->cols_d = (int64_t)h.cols[1].size();
+    info->minors_u = (int64_t)h.tree.minor_rows[0].size(); info->minors_d = (int64_t)h.tree.minor_rows[1].size();
+    info->tree_nodes = (int64_t)h.tree.factors.size();
+    info->egraph_classes = h.eg.A.classes + h.eg.B.classes;
+    info->egraph_nodes = h.eg.A.enodes + h.eg.B.enodes;
+    info->flops_per_site = h.algo == MBC_ALGO_DIRECT ? h.flops_direct : (h.algo == MBC_ALGO_TREE ? h.flops_tree : h.flops_egraph);
+    info->direct_flops_per_site = h.flops_direct;
+    info->scratch_bytes_per_site = h.algo == MBC_ALGO_TREE ? (int64_t)(h.tree.minor_rows[0].size() + h.tree.minor_rows[1].size()) * 16 : 32;
+    return MBC_OK;
+}
+
+mbc_status mbc_plan_get_tree(const mbc_plan* P, int64_t* n_nodes, int64_t* n_leaves, int32_t* factors, int32_t* children,
+                             double* coefficients) {
+    if (!P || !n_nodes || !n_leaves) return MBC_INVALID_ARG;
+    const TreePlan& t = P->hp.tree;
+    *n_nodes = (int64_t)t.factors.size();
+    *n_leaves = (int64_t)t.coefficients.size();
+    if (factors) std::memcpy(factors, t.factors.data(), t.factors.size() * sizeof(int32_t));
+    if (children) std::memcpy(children, t.children.data(), t.children.size() * sizeof(int32_t));
+    if (coefficients)
+        for (size_t i = 0; i < t.coefficients.size(); ++i) { coefficients[2 * i] = t.coefficients[i].real(); coefficients[2 * i + 1] = t.coefficients[i].imag(); }
+    return MBC_OK;
+}
+
+mbc_status mbc_plan_get_minor(const mbc_plan* P, int flavour, int64_t m, int8_t* rows, int8_t* cols) {
+    if (!P || flavour < 0 || flavour > 1 || !rows || !cols) return MBC_INVALID_ARG;
+    const TreePlan& t = P->hp.tree;
+    if (m < 0 || m >= (int64_t)t.minor_rows[flavour].size()) return MBC_INVALID_ARG;
+    mask_list(t.minor_rows[flavour][m], rows);
+    mask_list(t.minor_cols[flavour][m], cols);
+    return MBC_OK;
+}
+
+mbc_status mbc_plan_save(const mbc_plan* P, const char* path) {
+    if (!P || !path) return MBC_INVALID_ARG;
+    std::string err = plan_write(P->hp, path);
+    if (!err.empty()) return fail(P->ctx, MBC_IO, err);
+    return MBC_OK;
+}
+
+mbc_status mbc_plan_load(mbc_ctx* ctx, const char* path, mbc_plan** out) {
+    if (!ctx) return MBC_INVALID_ARG;
+    if (!path || !out) return fail(ctx, MBC_INVALID_ARG, "null path or output");
+    mbc_plan* P = new (std::nothrow) mbc_plan();
+    if (!P) return fail(ctx, MBC_OOM, "host allocation");
+    P->ctx = ctx;
+    std::string err;
+    try { err = plan_read(P->hp, path); } catch (const std::bad_alloc&) { err = "host allocation while reading"; }
+    if (!err.empty()) { delete P; return fail(ctx, MBC_IO, err); }
+    return finish_plan(ctx, P, out);
+}
+
+mbc_status mbc_correlator(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int64_t V3, void* C, void* site_out,
+                          mbc_stream stream) {
+    if (!P) return MBC_INVALID_ARG;
+    mbc_ctx* c = P->ctx;
+    if (n_sets < 0 || T < 0 || V3 < 0) return fail(c, MBC_INVALID_ARG, "negative size");
+    if (!C && (int64_t)n_sets * T > 0) return fail(c, MBC_INVALID_ARG, "null output");
+    if ((!U || !D) && (int64_t)n_sets * T * V3 > 0) return fail(c, MBC_INVALID_ARG, "null propagator field");
+    if ((int64_t)n_sets * T * V3 > ((int64_t)1 << 32)) return fail(c, MBC_UNSUPPORTED, "more than 2^32 sites in one call");
+    mbc_status st = run(P, U, D, n_sets, T, V3, C, site_out, (cudaStream_t)stream);
+    if (st == MBC_OK) c->err.clear();
+    return st;
+}
+
+mbc_status mbc_correlator_host(mbc_plan* P, const void* U_host, const void* D_host, int n_sets, int T, int64_t V3,
+                               void* C_host, mbc_stream stream) {
+    if (!P) return MBC_INVALID_ARG;
+    mbc_ctx* c = P->ctx;
+    if (n_sets < 0 || T < 0 || V3 < 0) return fail(c, MBC_INVALID_ARG, "negative size");
+    const int64_t n_sites = (int64_t)n_sets * T * V3;
+    if (!C_host || (n_sites && (!U_host || !D_host))) return fail(c, MBC_INVALID_ARG, "null host buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
+    cudaSetDevice(c->device);
+    const size_t fb = sizeof(double) * 288 * (size_t)n_sites, cb = sizeof(double2) * (size_t)n_sets * T;
+    mbc_status st = ensure(c, c->hU, fb, s);
+    if (st == MBC_OK) st = ensure(c, c->hD, fb, s);
+    if (st == MBC_OK) st = ensure(c, c->hC, cb, s);
+    if (st != MBC_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (fb) {
+        e = cudaMemcpyAsync(c->hU.p, U_host, fb, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->hD.p, D_host, fb, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "host to device copy");
+    }
+    st = run(P, c->hU.p, c->hD.p, n_sets, T, V3, c->hC.p, nullptr, s);
+    if (st != MBC_OK) return st;
+    if (cb) {
+        e = cudaMemcpyAsync(C_host, c->hC.p, cb, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "device to host copy");
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+    c->err.clear();
+    return MBC_OK;
+}
+
+mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
+    if (!c || (n_items && !items) || n_items < 0) return c ? fail(c, MBC_INVALID_ARG, "bad items") : MBC_INVALID_ARG;
+    if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
+    int64_t sites = 0;
+    for (int i = 0; i < n_items; ++i) sites = std::max<int64_t>(sites, (int64_t)items[i].n_sets * items[i].T * items[i].V3);
+    mbc_status st = ensure(c, c->partials, sizeof(d4) * (size_t)std::max<int64_t>(sites, 1), nullptr);
+    if (st == MBC_OK) st = ensure(c, c->site_tmp, sizeof(d4) * (size_t)std::max<int64_t>(sites, 1), nullptr);
+    if (st == MBC_OK) st = ensure(c, c->counter, 256, nullptr);
+    return st;
+}
+
+mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream stream) {
+    if (!c) return MBC_INVALID_ARG;
+    if (n_items < 0 || (n_items && !items)) return fail(c, MBC_INVALID_ARG, "bad items");
+    for (int i = 0; i < n_items; ++i) {
+        if (!items[i].plan || items[i].plan->ctx != c) return fail(c, MBC_INVALID_ARG, "item plan of another context");
+        if (items[i].plan->hp.algo != MBC_ALGO_EGRAPH) return fail(c, MBC_UNSUPPORTED, "batched items must use MBC_ALGO_EGRAPH");
+    }
+    for (int i = 0; i < n_items; ++i) {
+        const mbc_work& w = items[i];
+        mbc_status st = mbc_correlator(w.plan, w.U, w.D, w.n_sets, w.T, w.V3, w.C, nullptr, stream);
+        if (st != MBC_OK) return st;
+    }
+    return MBC_OK;
+}
+
+mbc_status mbc_set_schedule(mbc_plan* P, const mbc_schedule* s) {
+    if (!P || !s) return MBC_INVALID_ARG;
+    if (s->threads < 32 || s->threads > 256 || s->threads % 32 || s->blocks_per_sm < 1 || s->blocks_per_sm > 32 || s->sites_per_unit < 1)
+        return fail(P->ctx, MBC_INVALID_ARG, "schedule out of range (threads 32..256, multiple of 32)");
+    P->sched = *s;
+    return MBC_OK;
+}
+
+mbc_status mbc_get_schedule(const mbc_plan* P, mbc_schedule* s) {
+    if (!P || !s) return MBC_INVALID_ARG;
+    *s = P->sched;
+    return MBC_OK;
+}
+
+mbc_status mbc_autotune(mbc_plan* P, const void* U, const void* D, int64_t n_sites, mbc_stream stream, mbc_schedule* best) {
+    if (!P) return MBC_INVALID_ARG;
+    mbc_ctx* c = P->ctx;
+    if (!U || !D || n_sites <= 0) return fail(c, MBC_INVALID_ARG, "autotune needs fields and a positive site count");
+    if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<mbc_schedule> cands;
+    const int smem = P->ed.smem_values * 16 + 1024;
+    for (int th : {128, 256})
+        for (int bps : {1, 2, 3, 4, 6, 8}) {
+            if (P->hp.algo == MBC_ALGO_EGRAPH && bps * smem > 220 * 1024) continue;
+            if (P->hp.algo != MBC_ALGO_EGRAPH && bps != 2) continue;
+            for (int spu : {1, 4}) {
+                if (P->hp.algo != MBC_ALGO_DIRECT && spu != 1) continue;
+                cands.push_back({th, bps, spu});
+            }
+        }
+    Buf C;
+    cudaError_t e = cudaMalloc(&C.p, sizeof(double2) * (size_t)n_sites);
+    if (e != cudaSuccess) return fail(c, MBC_OOM, "autotune output");
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best_ms = -1.f;
+    mbc_schedule keep = P->sched;
+    for (auto& cand : cands) {
+        P->sched = cand;
+        mbc_status st = run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);   // warm-up (and pool growth)
+        if (st != MBC_OK) { cudaFree(C.p); return st; }
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 3; ++r) run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (best_ms < 0 || ms < best_ms) { best_ms = ms; keep = cand; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(C.p);
+    P->sched = keep;
+    c->tune_cache[P->signature] = keep;
+    if (best) *best = keep;
+    return MBC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// device.cuh - device-side views of a plan and the launch interfaces between the
+// C ABI (api.cu) and the kernel files (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "numeric.cuh"
+
+namespace mbc {
+
+// Work geometry shared by every algorithm: n_sets x T x V3 sites, fields laid out
+// [set][t][site][12][12] complex double; a "site" below is the flat index
+// (set * T + t) * V3 + x.
+struct Geometry {
+    int n_sets, T;
+    int64_t V3;
+    __host__ __device__ int64_t n_sites() const { return (int64_t)n_sets * T * V3; }
+};
+
+// Partial sums: one per (site, chunk); each holds a compensated complex double
+// (re.hi, re.lo, im.hi, im.lo).
+struct Partials {
+    d4* part;          // [n_sites * n_chunks]
+    int n_chunks;
+};
+
+// ---------------------------------------------------------------- direct sweep
+struct DirectDev {
+    int n_u, n_d;
+    int explicit_terms;
+    // factored: blocks of sink range x source range with coefficient P
+    int n_blocks;
+    const int64_t* blk_start;      // [n_blocks + 1] prefix sums of pairs
+    const int64_t* blk_s0; const int64_t* blk_r0; const int64_t* blk_nr;
+    const cd* blk_p;
+    const int8_t* snk_idx; const cd* snk_w;
+    const int8_t* src_idx; const cd* src_w;
+    // explicit: term t = (ex_snk[t], ex_src[t], ex_w[t])
+    const int8_t* ex_snk; const int8_t* ex_src; const cd* ex_w;
+    int64_t index_size;
+};
+
+// ---------------------------------------------------------------- factor tree
+struct TreeDev {
+    int n_u, n_d;
+    int64_t n_minors[2];
+    const int8_t* minor_rows[2];   // [m][n_f]
+    const int8_t* minor_cols[2];
+    int64_t n_nodes;
+    const int32_t* factors;
+    const int32_t* children;
+    const cd* coefficients;
+    int n_chunks;
+    const int64_t* chunk_node;
+    const int64_t* chunk_leaf;
+    const int32_t* chunk_count;
+};
+
+// ---------------------------------------------------------------- e-graph plan
+struct MinorDev {
+    int n;
+    int size[7];                   // |F_k|, k = 0..6 (size[0] = 1)
+    int off[7];                    // offset of level k in a stacked table
+    const uint16_t* child[7];      // [e * k + i]
+    const uint8_t* row[7];
+    int n_nodes;
+    const uint8_t* node_level;
+    const uint8_t* node_col;
+    const int8_t* node_sign;
+    const int32_t* node_leaf;
+};
+
+struct EgraphDev {
+    int flav_a, n_j;
+    MinorDev A, B;
+    int cache_level, n_cache_nodes, n_cache_slots;
+    const int32_t* cache_nodes;      // B node ids (levels <= L) in DFS order
+    const int32_t* cache_slot;       // per cache node: slot or -1
+    const int32_t* bcol_slot;
+    const uint8_t* bcol_path_col;
+    const int8_t* bcol_path_sign;
+    int n_rows_b;
+    const int32_t* g_off; const int32_t* g_j; const int32_t* g_a; const cd* g_w;
+    const int32_t* pair_off; const int32_t* pair_b; const cd* pair_coef;
+    int stack_a;                     // values in the A stack (levels 0..n_A)
+    int stack_b;                     // values in the B stack (levels 0..L-1)
+    int path_b;                      // values of one on-demand B column (levels L+1..n_B)
+    int n_batch;                     // B columns evaluated together
+    int smem_values;                 // total complex values in dynamic shared memory
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_direct(const DirectDev& d, int prec, const double* U, const double* D, Geometry g,
+                          int64_t chunk, Partials out, int threads, cudaStream_t s, int64_t* launches);
+cudaError_t launch_tree(const TreeDev& d, int prec, const double* U, const double* D, Geometry g,
+                        void* scratch, int64_t scratch_sites, int* exps, Partials out, int threads,
+                        cudaStream_t s, int64_t* launches);
+size_t tree_value_bytes(int prec);
+cudaError_t launch_egraph(const EgraphDev& d, int prec, const double* U, const double* D, Geometry g,
+                          Partials out, int threads, int blocks_per_sm, unsigned int* counter,
+                          cudaStream_t s, int64_t* launches);
+size_t egraph_smem_bytes(const EgraphDev& d, int prec);
+cudaError_t launch_reduce(Partials in, Geometry g, cd scale, double2* C, double2* site_out, d4* site_tmp,
+                          cudaStream_t s, int64_t* launches);
+
+}  // namespace mbc

@@ -1,0 +1,288 @@
+"""GPU parity of libmbc against the oracle (needs a CUDA GPU; marked gpu).
+
+Every test calls the library through its C ABI (the ctypes binding) on device buffers
+and compares with the oracle on the same seeded inputs: full-lattice C(t) where the
+oracle finishes in seconds, sampled per-site values at the paper's full sizes.
+Tolerances are the stated targets: 1e-12 relative for FP64, 1e-5 for the mixed
+arithmetic (plus a tighter 1e-9 check of the double-float design where it applies).
+"""
+import numpy as np
+import pytest
+
+import mbc_inputs as mi
+from oracle import correlator as ocor
+from oracle import native as onat
+from oracle import operators as oops
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-5}
+TIGHT_MIXED = 1e-9
+ALGOS = ("direct", "tree", "egraph")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_04269_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run(plan, U, D):
+    """U, D numpy [n_sets, T, V3, 12, 12] -> (C [n_sets, T], per-site [n_sets, T, V3])."""
+    n_sets, T, V3 = U.shape[:3]
+    Ud, Dd = dev(U), dev(D)
+    C = torch.zeros(n_sets, T, dtype=torch.complex128, device="cuda")
+    S = torch.zeros(n_sets, T, V3, dtype=torch.complex128, device="cuda")
+    plan.correlator(Ud, Dd, C, S)
+    torch.cuda.synchronize()
+    return C.cpu().numpy(), S.cpu().numpy()
+
+
+def relerr(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def check(got, ref, prec):
+    e = relerr(got, ref)
+    assert e <= TOL[prec], f"relative error {e:.3e} > {TOL[prec]}"
+    if prec == "mixed":
+        assert e <= TIGHT_MIXED, f"double-float error {e:.3e} above {TIGHT_MIXED}"
+    return e
+
+
+oracle_cache = {}
+
+
+def oracle_plan(name):
+    if name not in oracle_cache:
+        oracle_cache[name] = ocor.CanonicalPlan(oops.build(name))
+    return oracle_cache[name]
+
+
+def oracle_sites(name, U, D):
+    return oracle_plan(name).site_values(U.reshape(-1, 12, 12), D.reshape(-1, 12, 12), n_threads=onat.max_threads())
+
+
+# ---------------------------------------------------------------------------- full lattice
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_proton_4x8_full(ctx, algo, prec):
+    U, D = mi.workload_fields("proton_4x8")
+    ref_sites = oracle_sites("proton", U, D).reshape(U.shape[:2])
+    ref = np.array([np.sum(r) for r in ref_sites])
+    # the definition (index-set sweep with LU) agrees with the canonical form
+    assert relerr(ocor.site_direct(oops.build("proton"), U.reshape(-1, 12, 12), D.reshape(-1, 12, 12)),
+                  ref_sites.ravel()) < 1e-12
+    plan = ctx.plan_operator("proton", algo, prec)
+    C, S = run(plan, U[None], D[None])
+    check(C[0], ref, prec)
+    check(S[0].ravel(), ref_sites.ravel(), prec)
+    plan.destroy()
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dinucleon_small_full(ctx, algo, prec):
+    """D_I on a 4^3 x 4 lattice: every site against the oracle."""
+    U, D = mi.workload_fields("dinucleon_16x32", L=4, T=4)
+    ref_sites = oracle_sites("dinucleon_I", U, D).reshape(U.shape[:2])
+    plan = ctx.plan_operator("dinucleon_I", algo, prec)
+    C, S = run(plan, U[None], D[None])
+    check(C[0], ref_sites.sum(axis=1), prec)
+    check(S[0], ref_sites, prec)
+    plan.destroy()
+
+
+# ---------------------------------------------------------------------------- full sizes, sampled
+def sample_sites(T, V3, per_t, seed=0):
+    rng = np.random.default_rng(seed)
+    return [(t, int(x)) for t in range(T) for x in rng.choice(V3, size=per_t, replace=False)]
+
+
+@pytest.mark.parametrize("algo", ["egraph", "tree"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dinucleon_16x32_sampled(ctx, algo, prec):
+    U, D = mi.workload_fields("dinucleon_16x32")
+    plan = ctx.plan_operator("dinucleon_I", algo, prec)
+    C, S = run(plan, U[None], D[None])
+    pts = sample_sites(32, 16 ** 3, 2)
+    ts, xs = np.array([p[0] for p in pts]), np.array([p[1] for p in pts])
+    ref = oracle_sites("dinucleon_I", U[ts, xs], D[ts, xs])
+    check(S[0][ts, xs], ref, prec)
+    assert relerr(C[0], S[0].sum(axis=1)) < 1e-12          # the site sum is the sum of sites
+    plan.destroy()
+
+
+def test_dinucleon_three_way_full_lattice(ctx):
+    """Direct sweep, factor tree and e-graph plan agree on the full 16^3 x 32 lattice
+    (two time slices: the direct sweep costs ~1e9 flop per site)."""
+    U, D = mi.workload_fields("dinucleon_16x32", t_list=[0, 31], T=32)
+    out = {}
+    for algo in ALGOS:
+        plan = ctx.plan_operator("dinucleon_I", algo, "fp64")
+        out[algo] = run(plan, U[None], D[None])[0][0]
+        plan.destroy()
+    assert relerr(out["tree"], out["direct"]) < 1e-12
+    assert relerr(out["egraph"], out["direct"]) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["he3_I", "he3_II_s"])
+@pytest.mark.parametrize("algo,prec,tsub", [("egraph", "mixed", None), ("egraph", "fp64", (0, 23, 47)),
+                                            ("tree", "mixed", (5, 40)), ("tree", "fp64", (11,))])
+def test_he3_24x48_sampled(ctx, name, algo, prec, tsub):
+    """3He at 24^3 x 48: the mixed e-graph path on the whole lattice (the benchmarked
+    launch), FP64 and the tree on selected time slices; sampled sites vs the oracle."""
+    T = 48
+    t_list = list(range(T)) if tsub is None else list(tsub)
+    U, D = mi.workload_fields("he3_24x48", t_list=t_list)
+    plan = ctx.plan_operator(name, algo, prec)
+    C, S = run(plan, U[None], D[None])
+    per_t = 1 if tsub is None else 6
+    pts = sample_sites(len(t_list), 24 ** 3, per_t, seed=len(t_list))
+    ts, xs = np.array([p[0] for p in pts]), np.array([p[1] for p in pts])
+    ref = oracle_sites(name, U[ts, xs], D[ts, xs])
+    check(S[0][ts, xs], ref, prec)
+    assert relerr(C[0], S[0].sum(axis=1)) < 1e-12
+    plan.destroy()
+
+
+@pytest.mark.parametrize("name,n_sites", [("dinucleon_I", 6), ("he3_I", 3), ("he3_II_s", 2)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_direct_sweep_sampled(ctx, name, n_sites, prec):
+    """The unoptimised index-set sweep on a few sites of the full-size workloads."""
+    wl = "dinucleon_16x32" if name == "dinucleon_I" else "he3_24x48"
+    U, D = mi.workload_fields(wl, t_list=[9], L=24 if wl == "he3_24x48" else 16)
+    U, D = U[:, :n_sites], D[:, :n_sites]
+    plan = ctx.plan_operator(name, "direct", prec)
+    C, S = run(plan, U[None], D[None])
+    ref = oracle_sites(name, U, D)
+    e = relerr(S[0].ravel(), ref)
+    assert e <= TOL[prec], e
+    plan.destroy()
+
+
+@pytest.mark.parametrize("name", ["dinucleon_II", "he3_II"])
+def test_vanishing_operators(ctx, name):
+    """The printed D_II and 3He_II are identically zero: tree and e-graph return exact
+    zeros, the direct sweep rounding residue only (normwise against D_I / 3He_I)."""
+    U, D = mi.workload_fields("proton_4x8", L=2, T=2)
+    for algo in ("tree", "egraph"):
+        plan = ctx.plan_operator(name, algo, "fp64")
+        C, S = run(plan, U[None], D[None])
+        assert np.all(C == 0) and np.all(S == 0)
+        plan.destroy()
+    if name == "dinucleon_II":
+        plan = ctx.plan_operator(name, "direct", "fp64")
+        C, S = run(plan, U[None, :, :2], D[None, :, :2])
+        ref = oracle_sites("dinucleon_I", U[:, :2], D[:, :2])
+        assert np.max(np.abs(S[0].ravel())) < 1e-10 * np.max(np.abs(ref))
+        plan.destroy()
+
+
+# ---------------------------------------------------------------------------- edge cases
+def test_empty_and_ragged_geometry(ctx):
+    plan = ctx.plan_operator("dinucleon_I", "egraph", "mixed")
+    U, D = mi.workload_fields("dinucleon_16x32", L=4, T=2)
+    # ragged V3 (not a multiple of 32 or of the block size)
+    C, S = run(plan, U[None, :, :37], D[None, :, :37])
+    ref = oracle_sites("dinucleon_I", U[:, :37], D[:, :37]).reshape(2, 37)
+    check(S[0], ref, "mixed")
+    # V3 = 0: C = 0
+    Z = np.zeros((1, 2, 0, 12, 12), complex)
+    C, S = run(plan, Z, Z)
+    assert np.all(C == 0)
+    # two sets in one call equal two separate calls
+    U2, D2 = mi.workload_fields("dinucleon_16x32", L=4, T=2, set_index=0)
+    U3 = np.stack([U2, U2[::-1].copy()])
+    D3 = np.stack([D2, D2[::-1].copy()])
+    C2, _ = run(plan, U3, D3)
+    Ca, _ = run(plan, U3[:1], D3[:1])
+    Cb, _ = run(plan, U3[1:], D3[1:])
+    assert np.array_equal(C2[0], Ca[0]) and np.array_equal(C2[1], Cb[0])
+    plan.destroy()
+
+
+@pytest.mark.parametrize("algo", ["direct", "tree"])
+def test_explicit_terms(ctx, algo):
+    """mbc_plan_from_terms on a random explicit index set (n_u = 3, n_d = 2)."""
+    rng = np.random.default_rng(21)
+    n = 300
+    sink = rng.integers(0, 12, size=(n, 5)).astype(np.int8)
+    source = rng.integers(0, 12, size=(n, 5)).astype(np.int8)
+    W = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    U, D = mi.workload_fields("proton_4x8", L=2, T=1)
+    plan = ctx.plan_terms(3, 2, sink, source, W, scale=1.0, algo=algo, prec="fp64")
+    C, S = run(plan, U[None], D[None])
+    # oracle: each term as its own free index with P = diag(W)
+    snk = [(sink[i:i + 1], np.ones(1, complex)) for i in range(n)]
+    src = [(source[i:i + 1], np.ones(1, complex)) for i in range(n)]
+    ref = onat.direct(3, 2, snk, src, np.diag(W), U.reshape(-1, 12, 12), D.reshape(-1, 12, 12))
+    # the oracle's direct applies the Wick sign of n = 5 (+1); the plan's scale is 1
+    assert relerr(S[0].ravel(), ref) < 1e-11
+    plan.destroy()
+
+
+def test_host_end_to_end_matches_device(ctx):
+    U, D = mi.workload_fields("proton_4x8")
+    plan = ctx.plan_operator("proton", "egraph", "mixed")
+    C, _ = run(plan, U[None], D[None])
+    Ch = torch.zeros(1, 8, dtype=torch.complex128).pin_memory()
+    plan.correlator_host(torch.from_numpy(U[None].copy()).pin_memory(), torch.from_numpy(D[None].copy()).pin_memory(), Ch)
+    assert np.array_equal(Ch.numpy(), C)
+    plan.destroy()
+
+
+def test_plan_file_and_determinism(ctx, tmp_path):
+    U, D = mi.workload_fields("dinucleon_16x32", L=4, T=4)
+    plan = ctx.plan_operator("dinucleon_I", "egraph", "fp64")
+    C1, S1 = run(plan, U[None], D[None])
+    C2, S2 = run(plan, U[None], D[None])
+    assert np.array_equal(C1, C2) and np.array_equal(S1, S2)      # bit-reproducible
+    p = str(tmp_path / "d.plan")
+    plan.save(p)
+    plan2 = ctx.load_plan(p)
+    C3, _ = run(plan2, U[None], D[None])
+    assert np.array_equal(C1, C3)
+    plan.destroy()
+    plan2.destroy()
+
+
+def test_batch_matches_separate_calls(ctx):
+    from paper_2201_04269_gb300 import abi
+    items, refs, keep = [], [], []
+    for name, wl in (("proton", "proton_4x8"), ("dinucleon_I", "dinucleon_16x32")):
+        U, D = mi.workload_fields(wl, L=4, T=3)
+        plan = ctx.plan_operator(name, "egraph", "mixed")
+        C, _ = run(plan, U[None], D[None])
+        Ud, Dd = dev(U[None]), dev(D[None])
+        Cb = torch.zeros(1, 3, dtype=torch.complex128, device="cuda")
+        keep += [plan, Ud, Dd, Cb]
+        items.append(dict(plan=plan.handle, U=Ud, D=Dd, C=Cb, n_sets=1, T=3, V3=64))
+        refs.append(C)
+    abi.mbc_batch_reserve(ctx.handle, items)
+    ctx.batch(items)
+    torch.cuda.synchronize()
+    for it, ref in zip(items, refs):
+        assert np.array_equal(it["C"].cpu().numpy(), ref)
+
+
+def test_autotune_keeps_results(ctx):
+    U, D = mi.workload_fields("dinucleon_16x32", L=4, T=4)
+    plan = ctx.plan_operator("dinucleon_I", "egraph", "mixed")
+    C1, _ = run(plan, U[None], D[None])
+    s = plan.autotune(dev(U), dev(D), U.shape[0] * U.shape[1])
+    assert s["threads"] in (128, 256) and s["blocks_per_sm"] >= 1
+    C2, _ = run(plan, U[None], D[None])
+    check(C2, C1, "mixed")
+    plan.destroy()
