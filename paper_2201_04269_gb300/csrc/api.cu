@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mbc.h"
+#include "mbc.h"
 #include "device.cuh"
 #include "plan.hpp"
 
@@ -99,6 +99,26 @@ struct Blob {
 
 template <class T> const T* at(void* base, size_t off) { return reinterpret_cast<const T*>(static_cast<unsigned char*>(base) + off); }
 
+// 16-byte device values of a precision: complex double, or complex double-float
+// (each part split into hi = float(x), lo = float(x - hi))
+struct Val16 { unsigned char b[16]; };
+std::vector<Val16> to_val(const std::vector<cplx>& v, int prec) {
+    std::vector<Val16> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (prec == 0) {
+            double x[2] = {v[i].real(), v[i].imag()};
+            std::memcpy(o[i].b, x, 16);
+        } else {
+            float x[4];
+            const double re = v[i].real(), im = v[i].imag();
+            x[0] = (float)re; x[1] = (float)(re - (double)x[0]);
+            x[2] = (float)im; x[3] = (float)(im - (double)x[2]);
+            std::memcpy(o[i].b, x, 16);
+        }
+    }
+    return o;
+}
+
 std::vector<cd> to_cd(const std::vector<cplx>& v) {
     std::vector<cd> o(v.size());
     for (size_t i = 0; i < v.size(); ++i) o[i] = cd_make(v[i].real(), v[i].imag());
@@ -118,18 +138,20 @@ mbc_status upload(mbc_plan* P) {
     HostPlan& h = P->hp;
     Blob b;
     // direct
-    std::vector<int64_t> blk_start(1, 0), blk_nr;
-    std::vector<cd> blk_p = to_cd(h.direct.blk_p);
+    std::vector<int64_t> blk_start(1, 0), blk_nr, blk_ns;
+    const int pr = h.prec;
+    std::vector<Val16> blk_p = to_val(h.direct.blk_p, pr);
     for (size_t i = 0; i < h.direct.blk_s0.size(); ++i) {
         int64_t ns = h.direct.blk_s1[i] - h.direct.blk_s0[i], nr = h.direct.blk_r1[i] - h.direct.blk_r0[i];
         blk_start.push_back(blk_start.back() + ns * nr);
         blk_nr.push_back(nr);
+        blk_ns.push_back(ns);
     }
     blk_start.push_back(INT64_MAX);   // sentinel: the block scan never runs past the end
-    size_t o_bs = b.add(blk_start), o_s0 = b.add(h.direct.blk_s0), o_r0 = b.add(h.direct.blk_r0), o_nr = b.add(blk_nr);
+    size_t o_bs = b.add(blk_start), o_s0 = b.add(h.direct.blk_s0), o_r0 = b.add(h.direct.blk_r0), o_nr = b.add(blk_nr), o_ns = b.add(blk_ns);
     size_t o_bp = b.add(blk_p);
-    size_t o_si = b.add(h.snk_idx), o_sw = b.add(to_cd(h.snk_w)), o_ri = b.add(h.src_idx), o_rw = b.add(to_cd(h.src_w));
-    size_t o_es = b.add(h.ex_snk), o_er = b.add(h.ex_src), o_ew = b.add(to_cd(h.ex_w));
+    size_t o_si = b.add(h.snk_idx), o_sw = b.add(to_val(h.snk_w, pr)), o_ri = b.add(h.src_idx), o_rw = b.add(to_val(h.src_w, pr));
+    size_t o_es = b.add(h.ex_snk), o_er = b.add(h.ex_src), o_ew = b.add(to_val(h.ex_w, pr));
     // tree
     std::vector<int8_t> mr[2], mc[2];
     int nf[2] = {h.n_u, h.n_d};
@@ -141,7 +163,7 @@ mbc_status upload(mbc_plan* P) {
             for (int i = 0; i < nf[f]; ++i) { mr[f].push_back(r[i]); mc[f].push_back(c[i]); }
         }
     size_t o_mr0 = b.add(mr[0]), o_mc0 = b.add(mc[0]), o_mr1 = b.add(mr[1]), o_mc1 = b.add(mc[1]);
-    size_t o_tf = b.add(h.tree.factors), o_tc = b.add(h.tree.children), o_tco = b.add(to_cd(h.tree.coefficients));
+    size_t o_tf = b.add(h.tree.factors), o_tc = b.add(h.tree.children), o_tco = b.add(to_val(h.tree.coefficients, pr));
     size_t o_cn = b.add(h.tree.chunk_node), o_cl = b.add(h.tree.chunk_leaf), o_cc = b.add(h.tree.chunk_count);
     // e-graph
     EgraphPlan& e = h.eg;
@@ -158,8 +180,8 @@ mbc_status upload(mbc_plan* P) {
     }
     size_t o_cnodes = b.add(e.cache_nodes), o_cslot = b.add(e.cache_slot_of_node), o_bslot = b.add(e.bcol_slot);
     size_t o_bpc = b.add(e.bcol_path_col), o_bps = b.add(e.bcol_path_sign);
-    size_t o_goff = b.add(e.g_off), o_gj = b.add(e.g_j), o_ga = b.add(e.g_a), o_gw = b.add(to_cd(e.g_w));
-    size_t o_poff = b.add(e.pair_off), o_pb = b.add(e.pair_b), o_pc = b.add(to_cd(e.pair_coef));
+    size_t o_goff = b.add(e.g_off), o_gj = b.add(e.g_j), o_ga = b.add(e.g_a), o_gw = b.add(to_val(e.g_w, pr));
+    size_t o_poff = b.add(e.pair_off), o_pb = b.add(e.pair_b), o_pc = b.add(to_val(e.pair_coef, pr));
 
     void* dev = nullptr;
     cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
@@ -175,9 +197,9 @@ mbc_status upload(mbc_plan* P) {
     dd.n_u = h.n_u; dd.n_d = h.n_d; dd.explicit_terms = h.explicit_terms;
     dd.n_blocks = (int)h.direct.blk_s0.size();
     dd.blk_start = at<int64_t>(dev, o_bs); dd.blk_s0 = at<int64_t>(dev, o_s0); dd.blk_r0 = at<int64_t>(dev, o_r0);
-    dd.blk_nr = at<int64_t>(dev, o_nr); dd.blk_p = at<cd>(dev, o_bp);
-    dd.snk_idx = at<int8_t>(dev, o_si); dd.snk_w = at<cd>(dev, o_sw); dd.src_idx = at<int8_t>(dev, o_ri); dd.src_w = at<cd>(dev, o_rw);
-    dd.ex_snk = at<int8_t>(dev, o_es); dd.ex_src = at<int8_t>(dev, o_er); dd.ex_w = at<cd>(dev, o_ew);
+    dd.blk_nr = at<int64_t>(dev, o_nr); dd.blk_ns = at<int64_t>(dev, o_ns); dd.blk_p = at<Val16>(dev, o_bp);
+    dd.snk_idx = at<int8_t>(dev, o_si); dd.snk_w = at<Val16>(dev, o_sw); dd.src_idx = at<int8_t>(dev, o_ri); dd.src_w = at<Val16>(dev, o_rw);
+    dd.ex_snk = at<int8_t>(dev, o_es); dd.ex_src = at<int8_t>(dev, o_er); dd.ex_w = at<Val16>(dev, o_ew);
     dd.index_size = h.direct.index_size;
 
     TreeDev& td = P->td;
@@ -186,7 +208,7 @@ mbc_status upload(mbc_plan* P) {
     td.minor_rows[0] = at<int8_t>(dev, o_mr0); td.minor_cols[0] = at<int8_t>(dev, o_mc0);
     td.minor_rows[1] = at<int8_t>(dev, o_mr1); td.minor_cols[1] = at<int8_t>(dev, o_mc1);
     td.n_nodes = (int64_t)h.tree.factors.size();
-    td.factors = at<int32_t>(dev, o_tf); td.children = at<int32_t>(dev, o_tc); td.coefficients = at<cd>(dev, o_tco);
+    td.factors = at<int32_t>(dev, o_tf); td.children = at<int32_t>(dev, o_tc); td.coefficients = at<Val16>(dev, o_tco);
     td.n_chunks = (int)h.tree.chunk_node.size();
     td.chunk_node = at<int64_t>(dev, o_cn); td.chunk_leaf = at<int64_t>(dev, o_cl); td.chunk_count = at<int32_t>(dev, o_cc);
 
@@ -210,20 +232,20 @@ mbc_status upload(mbc_plan* P) {
     ed.cache_nodes = at<int32_t>(dev, o_cnodes); ed.cache_slot = at<int32_t>(dev, o_cslot); ed.bcol_slot = at<int32_t>(dev, o_bslot);
     ed.bcol_path_col = at<uint8_t>(dev, o_bpc); ed.bcol_path_sign = at<int8_t>(dev, o_bps);
     ed.n_rows_b = e.B.n ? (int)e.B.level_rows[e.B.n].size() : 1;
-    ed.g_off = at<int32_t>(dev, o_goff); ed.g_j = at<int32_t>(dev, o_gj); ed.g_a = at<int32_t>(dev, o_ga); ed.g_w = at<cd>(dev, o_gw);
-    ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_coef = at<cd>(dev, o_pc);
+    ed.g_off = at<int32_t>(dev, o_goff); ed.g_j = at<int32_t>(dev, o_gj); ed.g_a = at<int32_t>(dev, o_ga); ed.g_w = at<Val16>(dev, o_gw);
+    ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_coef = at<Val16>(dev, o_pc);
     ed.stack_a = ed.A.off[ed.A.n] + ed.A.size[ed.A.n];
     ed.stack_b = e.B.n ? ed.B.off[L] : 0;
     ed.path_b = 0;
     for (int k = L + 1; k <= e.B.n; ++k) ed.path_b += ed.B.size[k];
     int max_pairs = 1;
     for (size_t i = 0; i + 1 < e.pair_off.size(); ++i) max_pairs = std::max(max_pairs, e.pair_off[i + 1] - e.pair_off[i]);
-    ed.n_batch = std::min(max_pairs, 8);
+    ed.n_batch = std::min(max_pairs, 4);
     auto smem_values = [&](int nbatch) {
         int fL = e.B.n ? ed.B.size[L] : 1;
-        return 288 + ed.stack_a + ed.stack_b + ed.n_cache_slots * fL + nbatch * ed.path_b + ed.n_j * ed.n_rows_b;
+        return 2 * kBlk + ed.stack_a + ed.stack_b + ed.n_cache_slots * fL + nbatch * ed.path_b + ed.n_j * ed.n_rows_b;
     };
-    while (ed.n_batch > 1 && smem_values(ed.n_batch) * 16 > 110 * 1024) --ed.n_batch;
+    while (ed.n_batch > 1 && smem_values(ed.n_batch) * 16 > 72 * 1024) --ed.n_batch;
     ed.smem_values = smem_values(ed.n_batch);
     return MBC_OK;
 }
@@ -267,7 +289,8 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
     P->signature = signature(h);
     auto it = ctx->tune_cache.find(P->signature);
     if (it != ctx->tune_cache.end()) P->sched = it->second;
-    else if (h.algo == MBC_ALGO_EGRAPH) P->sched.blocks_per_sm = std::max(1, std::min(4, (int)(200 * 1024 / (P->ed.smem_values * 16 + 1024))));
+    else if (h.algo == MBC_ALGO_EGRAPH)   // as many blocks per SM as shared memory allows
+        P->sched.blocks_per_sm = std::max(1, std::min(8, (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024))));
     ctx->plans.push_back(P);
     *out = P;
     ctx->err.clear();

@@ -58,13 +58,16 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 template <class P>
 __device__ __forceinline__ void load_pair(const double* __restrict__ a, const double* __restrict__ b,
                                           typename P::V* sa, typename P::V* sb, double* red, int& ea, int& eb) {
+    // entry (r, c) goes to [r * kLd + c]
     cd* ra = reinterpret_cast<cd*>(sa);
     cd* rb = reinterpret_cast<cd*>(sb);
     double ma = 0.0, mb = 0.0;
     for (int i = threadIdx.x; i < 288; i += blockDim.x) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(i < 144 ? a : b) + (i < 144 ? i : i - 144));
-        if (i < 144) { ra[i] = cd_make(v.x, v.y); ma = fmax(ma, fmax(fabs(v.x), fabs(v.y))); }
-        else { rb[i - 144] = cd_make(v.x, v.y); mb = fmax(mb, fmax(fabs(v.x), fabs(v.y))); }
+        const int e = i < 144 ? i : i - 144;
+        const int o = (e / 12) * kLd + e % 12;
+        const double2 v = __ldg(reinterpret_cast<const double2*>(i < 144 ? a : b) + e);
+        if (i < 144) { ra[o] = cd_make(v.x, v.y); ma = fmax(ma, fmax(fabs(v.x), fabs(v.y))); }
+        else { rb[o] = cd_make(v.x, v.y); mb = fmax(mb, fmax(fabs(v.x), fabs(v.y))); }
     }
     if (!P::scaled()) { ea = eb = 0; __syncthreads(); return; }
     ma = block_max(ma, red);
@@ -72,8 +75,10 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ a, const do
     ea = block_exponent(ma);
     eb = block_exponent(mb);
     for (int i = threadIdx.x; i < 288; i += blockDim.x) {
-        if (i < 144) sa[i] = P::from_cd(ra[i], -ea);
-        else sb[i - 144] = P::from_cd(rb[i - 144], -eb);
+        const int e = i < 144 ? i : i - 144;
+        const int o = (e / 12) * kLd + e % 12;
+        if (i < 144) sa[o] = P::from_cd(ra[o], -ea);
+        else sb[o] = P::from_cd(rb[o], -eb);
     }
     __syncthreads();
 }
@@ -81,15 +86,16 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ a, const do
 // --------------------------------------------------------------------- LU determinants
 // det of the N x N matrix m[rows[i]][cols[k]] gathered from a 12x12 block, by Gaussian
 // elimination with partial pivoting (pivot = largest |re| + |im|, first on ties; a row
-// swap flips the sign; an exactly zero pivot gives 0).
-template <class P, int N>
+// swap flips the sign; an exactly zero pivot gives 0, and so does, in the mixed
+// arithmetic, a pivot below P::tiny()).
+template <class P, int N, int LD>
 __device__ __forceinline__ typename P::V det_gather(const typename P::V* m, const int8_t* rows, const int8_t* cols) {
     typedef typename P::V V;
     V a[N][N];
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int k = 0; k < N; ++k) a[i][k] = m[rows[i] * 12 + cols[k]];
+        for (int k = 0; k < N; ++k) a[i][k] = m[rows[i] * LD + cols[k]];
     V det = P::zero();
     bool first = true;
     int sign = 1;
@@ -102,7 +108,7 @@ __device__ __forceinline__ typename P::V det_gather(const typename P::V* m, cons
             auto mg = P::mag(a[i][k]);
             if (mg > best) { best = mg; p = i; }
         }
-        if (best == 0) return P::zero();
+        if (best <= P::tiny()) return P::zero();
 #pragma unroll
         for (int i = k + 1; i < N; ++i) {
             if (i == p) {
@@ -114,9 +120,7 @@ __device__ __forceinline__ typename P::V det_gather(const typename P::V* m, cons
         det = first ? a[k][k] : P::mul(det, a[k][k]);
         first = false;
         if (k + 1 < N) {
-            V one = P::zero();
-            one = P::from_cd(cd_make(1.0, 0.0), 0);
-            V inv = P::div(one, a[k][k]);
+            V inv = P::div(P::one(), a[k][k]);
 #pragma unroll
             for (int i = k + 1; i < N; ++i) {
                 V f = P::mul(a[i][k], inv);
@@ -134,16 +138,16 @@ __device__ __forceinline__ typename P::V det_gather(const typename P::V* m, cons
     return sign < 0 ? P::neg(det) : det;
 }
 
-template <class P>
+template <class P, int LD>
 __device__ __forceinline__ typename P::V det_n(int n, const typename P::V* m, const int8_t* rows, const int8_t* cols) {
     switch (n) {
-        case 1: return m[rows[0] * 12 + cols[0]];
-        case 2: return det_gather<P, 2>(m, rows, cols);
-        case 3: return det_gather<P, 3>(m, rows, cols);
-        case 4: return det_gather<P, 4>(m, rows, cols);
-        case 5: return det_gather<P, 5>(m, rows, cols);
-        case 6: return det_gather<P, 6>(m, rows, cols);
-        default: return P::from_cd(cd_make(1.0, 0.0), 0);   // n = 0: empty product
+        case 1: return m[rows[0] * LD + cols[0]];
+        case 2: return det_gather<P, 2, LD>(m, rows, cols);
+        case 3: return det_gather<P, 3, LD>(m, rows, cols);
+        case 4: return det_gather<P, 4, LD>(m, rows, cols);
+        case 5: return det_gather<P, 5, LD>(m, rows, cols);
+        case 6: return det_gather<P, 6, LD>(m, rows, cols);
+        default: return P::one();   // n = 0: empty product
     }
 }
 

@@ -8,6 +8,11 @@
 
 namespace mbc {
 
+// Shared-memory leading dimension of a staged 12x12 block: 13 values per row so that
+// 16-byte reads of one column by 8 consecutive rows hit 8 different bank groups.
+static constexpr int kLd = 13;
+static constexpr int kBlk = 12 * kLd;
+
 // Work geometry shared by every algorithm: n_sets x T x V3 sites, fields laid out
 // [set][t][site][12][12] complex double; a "site" below is the flat index
 // (set * T + t) * V3 + x.
@@ -31,12 +36,13 @@ struct DirectDev {
     // factored: blocks of sink range x source range with coefficient P
     int n_blocks;
     const int64_t* blk_start;      // [n_blocks + 1] prefix sums of pairs
-    const int64_t* blk_s0; const int64_t* blk_r0; const int64_t* blk_nr;
-    const cd* blk_p;
-    const int8_t* snk_idx; const cd* snk_w;
-    const int8_t* src_idx; const cd* src_w;
+    const int64_t* blk_s0; const int64_t* blk_r0; const int64_t* blk_nr; const int64_t* blk_ns;
+    // weights below are 16-byte values of the plan's precision (cd or cdf)
+    const void* blk_p;
+    const int8_t* snk_idx; const void* snk_w;
+    const int8_t* src_idx; const void* src_w;
     // explicit: term t = (ex_snk[t], ex_src[t], ex_w[t])
-    const int8_t* ex_snk; const int8_t* ex_src; const cd* ex_w;
+    const int8_t* ex_snk; const int8_t* ex_src; const void* ex_w;
     int64_t index_size;
 };
 
@@ -49,7 +55,7 @@ struct TreeDev {
     int64_t n_nodes;
     const int32_t* factors;
     const int32_t* children;
-    const cd* coefficients;
+    const void* coefficients;      // precision-P values
     int n_chunks;
     const int64_t* chunk_node;
     const int64_t* chunk_leaf;
@@ -80,8 +86,8 @@ struct EgraphDev {
     const uint8_t* bcol_path_col;
     const int8_t* bcol_path_sign;
     int n_rows_b;
-    const int32_t* g_off; const int32_t* g_j; const int32_t* g_a; const cd* g_w;
-    const int32_t* pair_off; const int32_t* pair_b; const cd* pair_coef;
+    const int32_t* g_off; const int32_t* g_j; const int32_t* g_a; const void* g_w;   // g_w, pair_coef:
+    const int32_t* pair_off; const int32_t* pair_b; const void* pair_coef;           // precision-P values
     int stack_a;                     // values in the A stack (levels 0..n_A)
     int stack_b;                     // values in the B stack (levels 0..L-1)
     int path_b;                      // values of one on-demand B column (levels L+1..n_B)

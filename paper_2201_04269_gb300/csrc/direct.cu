@@ -20,8 +20,8 @@ __global__ void __launch_bounds__(256) direct_kernel(DirectDev d, const double* 
                                                      const double* __restrict__ D, Geometry g, int64_t chunk,
                                                      Partials out) {
     typedef typename P::V V;
-    __shared__ __align__(16) V su[144];
-    __shared__ __align__(16) V sd[144];
+    __shared__ __align__(16) V su[kBlk];
+    __shared__ __align__(16) V sd[kBlk];
     __shared__ double red[4 * 32];
     const int nq = d.n_u + d.n_d;
     const int64_t n_chunks = out.n_chunks;
@@ -34,34 +34,56 @@ __global__ void __launch_bounds__(256) direct_kernel(DirectDev d, const double* 
         const int64_t end = min(begin + chunk, d.index_size);
         typename P::A acc;
         P::acc_zero(acc);
+        // pair q = blk_start[blk] + (a - s0) * nr + (r - r0): the thread steps (blk, a, r)
+        // by blockDim without dividing
         int blk = 0;
-        for (int64_t q = begin + threadIdx.x; q < end; q += blockDim.x) {
+        int64_t a = 0, r = 0, nr = 1;
+        const int64_t q0 = begin + threadIdx.x;
+        if (!d.explicit_terms && q0 < end) {
+            while (q0 >= d.blk_start[blk + 1]) ++blk;
+            const int64_t loc = q0 - d.blk_start[blk];
+            nr = d.blk_nr[blk];
+            a = d.blk_s0[blk] + loc / nr;
+            r = d.blk_r0[blk] + loc % nr;
+        }
+        for (int64_t q = q0; q < end; q += blockDim.x) {
             const int8_t* ia;
             const int8_t* ib;
-            cd w;
+            V w;
             if (d.explicit_terms) {
                 ia = d.ex_snk + q * nq;
                 ib = d.ex_src + q * nq;
-                w = d.ex_w[q];
+                w = ldv<V>(d.ex_w, q);
             } else {
-                while (q >= d.blk_start[blk + 1]) ++blk;      // q only grows within a thread
-                const int64_t loc = q - d.blk_start[blk];
-                const int64_t a = d.blk_s0[blk] + loc / d.blk_nr[blk];
-                const int64_t r = d.blk_r0[blk] + loc % d.blk_nr[blk];
                 ia = d.snk_idx + a * nq;
                 ib = d.src_idx + r * nq;
-                const cd p = d.blk_p[blk], s = d.snk_w[a], t = d.src_w[r];
-                const cd ps = cd_make(p.re * s.re - p.im * s.im, p.re * s.im + p.im * s.re);
-                w = cd_make(ps.re * t.re + ps.im * t.im, ps.im * t.re - ps.re * t.im);   // p s conj(t)
+                // W = P_jj' s_j(a) conj(r_j'(a'))
+                w = P::mul(P::mul(ldv<V>(d.blk_p, blk), ldv<V>(d.snk_w, a)), conj(ldv<V>(d.src_w, r)));
+                // advance by blockDim pairs
+                int64_t step = blockDim.x;
+                while (step > 0) {
+                    const int64_t room = (d.blk_r0[blk] + nr) - r;     // pairs left in this row of the block
+                    if (step < room) { r += step; step = 0; break; }
+                    step -= room;
+                    ++a;
+                    r = d.blk_r0[blk];
+                    if (a - d.blk_s0[blk] >= d.blk_ns[blk]) {   // next block
+                        ++blk;
+                        if (blk >= d.n_blocks) break;
+                        nr = d.blk_nr[blk];
+                        a = d.blk_s0[blk];
+                        r = d.blk_r0[blk];
+                    }
+                }
             }
             int8_t ra[12], rb[12];
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
                 if (i < nq) { ra[i] = ia[i]; rb[i] = ib[i]; }
             }
-            const V du = det_n<P>(d.n_u, su, ra, rb);
-            const V dd = det_n<P>(d.n_d, sd, ra + d.n_u, rb + d.n_u);
-            const V wd = P::mul(P::from_cd(w, 0), du);
+            const V du = det_n<P, kLd>(d.n_u, su, ra, rb);
+            const V dd = det_n<P, kLd>(d.n_d, sd, ra + d.n_u, rb + d.n_u);
+            const V wd = P::mul(w, du);
             P::fma(acc, wd, dd);
         }
         const cd v = P::to_cd(P::get(acc));

@@ -36,7 +36,7 @@ __device__ __forceinline__ void laplace_level(const MinorDev& m, int k, int col,
         for (int i = 0; i < k; ++i) {
             const int r = __ldg(row + e * k + i);
             const int c = __ldg(child + e * k + i);
-            const typename P::V a = mat[r * 12 + col];
+            const typename P::V a = mat[r * kLd + col];
             if (((i & 1) ? -sign : sign) > 0) P::fma(acc, a, parent[c]);
             else P::fms(acc, a, parent[c]);
         }
@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
     typedef typename P::V V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* sA = reinterpret_cast<V*>(smem_raw);
-    V* sB = sA + 144;
-    V* stA = sB + 144;
+    V* sB = sA + kBlk;
+    V* stA = sB + kBlk;
     V* stB = stA + d.stack_a;
     const int L = d.cache_level;
     const int nA = d.A.n, nB = d.B.n;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
     __shared__ unsigned int s_unit;
     const int64_t n_units = g.n_sites();
     const int n_rb = d.n_rows_b;
-    const V one = P::from_cd(cd_make(1.0, 0.0), 0);
+    const V one = P::one();
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
         __syncthreads();
@@ -101,16 +101,21 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
             if (leaf < 0) continue;
             const V* T = stA + d.A.off[nA];
             // G_j(R_b) = sum_{R_a} s_j(R_a, R_b) T(R_a)
-            for (int it = threadIdx.x; it < n_rb * d.n_j; it += blockDim.x) {
-                const int b = it / d.n_j, j = it - b * d.n_j;
-                typename P::A gj;
-                P::acc_zero(gj);
-                const int e1 = __ldg(d.g_off + it + 1);
-                for (int e = __ldg(d.g_off + it); e < e1; ++e) {
-                    const double2 w = __ldg(reinterpret_cast<const double2*>(d.g_w) + e);
-                    P::fma(gj, P::from_cd(cd_make(w.x, w.y), 0), T[__ldg(d.g_a + e)]);
+            {
+                // flat index it = b * n_j + j, stepped without division
+                const int nj = d.n_j, total = n_rb * nj, stride = blockDim.x;
+                int b = threadIdx.x / nj, j = threadIdx.x - (threadIdx.x / nj) * nj;
+                const int db = stride / nj, dj = stride - db * nj;
+                for (int it = threadIdx.x; it < total; it += stride) {
+                    typename P::A gj;
+                    P::acc_zero(gj);
+                    const int e1 = __ldg(d.g_off + it + 1);
+                    for (int e = __ldg(d.g_off + it); e < e1; ++e) P::fma(gj, ldv<V>(d.g_w, e), T[__ldg(d.g_a + e)]);
+                    G[j * n_rb + b] = P::get(gj);
+                    b += db;
+                    j += dj;
+                    if (j >= nj) { j -= nj; ++b; }
                 }
-                G[j * n_rb + b] = P::get(gj);
             }
             __syncthreads();
             // paired B columns, in batches
@@ -124,8 +129,10 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
                         const int ppar = k - 1 == L ? -1 : d.B.off[k - 1] - d.B.off[L + 1];
                         const uint16_t* child = d.B.child[k];
                         const uint8_t* row = d.B.row[k];
+                        // flat index it = bi * fk + e, stepped without division
+                        int bi = threadIdx.x / fk, e = threadIdx.x - (threadIdx.x / fk) * fk;
+                        const int dbi = blockDim.x / fk, de = blockDim.x - dbi * fk;
                         for (int it = threadIdx.x; it < nbt * fk; it += blockDim.x) {
-                            const int bi = it / fk, e = it - bi * fk;
                             const int cb = __ldg(d.pair_b + ps + bi);
                             const int step = (int)((int64_t)cb * (nB - L) + (k - L - 1));
                             const V* parent = ppar < 0 ? cache + (size_t)__ldg(d.bcol_slot + cb) * fL
@@ -137,19 +144,23 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
                             for (int i = 0; i < k; ++i) {
                                 const int r = __ldg(row + e * k + i);
                                 const int c = __ldg(child + e * k + i);
-                                const V m = sB[r * 12 + col];
+                                const V m = sB[r * kLd + col];
                                 if (((i & 1) ? -sign : sign) > 0) P::fma(a, m, parent[c]);
                                 else P::fms(a, m, parent[c]);
                             }
                             path[(size_t)bi * d.path_b + poff + e] = P::get(a);
+                            bi += dbi;
+                            e += de;
+                            if (e >= fk) { e -= fk; ++bi; }
                         }
                         __syncthreads();
                     }
                 }
                 // accumulate: threads over (pair, R_b)
                 const int last = nB > L ? d.B.off[nB] - d.B.off[L + 1] : 0;
+                int bi = threadIdx.x / n_rb, b = threadIdx.x - (threadIdx.x / n_rb) * n_rb;
+                const int dbi = blockDim.x / n_rb, db = blockDim.x - dbi * n_rb;
                 for (int it = threadIdx.x; it < nbt * n_rb; it += blockDim.x) {
-                    const int bi = it / n_rb, b = it - bi * n_rb;
                     const int pr = ps + bi;
                     const int cb = __ldg(d.pair_b + pr);
                     V bv;
@@ -158,11 +169,11 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
                     else bv = path[(size_t)bi * d.path_b + last + b];
                     typename P::A h;
                     P::acc_zero(h);
-                    for (int j = 0; j < d.n_j; ++j) {
-                        const double2 c = __ldg(reinterpret_cast<const double2*>(d.pair_coef) + (size_t)pr * d.n_j + j);
-                        P::fma(h, P::from_cd(cd_make(c.x, c.y), 0), G[j * n_rb + b]);
-                    }
+                    for (int j = 0; j < d.n_j; ++j) P::fma(h, ldv<V>(d.pair_coef, (int64_t)pr * d.n_j + j), G[j * n_rb + b]);
                     P::fma(acc, P::get(h), bv);
+                    bi += dbi;
+                    b += db;
+                    if (b >= n_rb) { b -= n_rb; ++bi; }
                 }
                 if (ps + d.n_batch < p1) __syncthreads();
             }

@@ -96,6 +96,7 @@ struct FP64 {
     typedef cd A;
     static constexpr int kind = 0;
     __device__ __forceinline__ static V zero() { return cd_make(0.0, 0.0); }
+    __device__ __forceinline__ static V one() { return cd_make(1.0, 0.0); }
     __device__ __forceinline__ static void acc_zero(A& a) { a.re = 0.0; a.im = 0.0; }
     __device__ __forceinline__ static void fma(A& a, V x, V y) {
         a.re = __fma_rn(x.re, y.re, a.re); a.re = __fma_rn(-x.im, y.im, a.re);
@@ -125,24 +126,34 @@ struct FP64 {
     __device__ __forceinline__ static V from_cd(cd x, int) { return x; }
     __device__ __forceinline__ static cd to_cd(V x) { return x; }
     __device__ __forceinline__ static bool scaled() { return false; }
+    // smallest pivot magnitude taken as nonzero by the LU
+    __device__ __forceinline__ static double tiny() { return 0.0; }
 };
 
 struct MIXED {
     typedef cdf V;
-    struct A { dacc re, im; };
+    // four independent chains (re: +x.re y.re and -x.im y.im; im: x.re y.im and x.im y.re)
+    // so that consecutive multiply-adds do not wait on each other
+    struct A { dacc r0, r1, i0, i1; };
     static constexpr int kind = 1;
     __device__ __forceinline__ static V zero() { V z; z.re.hi = z.re.lo = z.im.hi = z.im.lo = 0.f; return z; }
-    __device__ __forceinline__ static void acc_zero(A& a) { dacc_zero(a.re); dacc_zero(a.im); }
+    __device__ __forceinline__ static V one() { V z = zero(); z.re.hi = 1.f; return z; }
+    __device__ __forceinline__ static void acc_zero(A& a) { dacc_zero(a.r0); dacc_zero(a.r1); dacc_zero(a.i0); dacc_zero(a.i1); }
     __device__ __forceinline__ static void fma(A& a, V x, V y) {
-        dacc_fma(a.re, x.re, y.re); dacc_fma(a.re, df_neg(x.im), y.im);
-        dacc_fma(a.im, x.re, y.im); dacc_fma(a.im, x.im, y.re);
+        dacc_fma(a.r0, x.re, y.re); dacc_fma(a.r1, df_neg(x.im), y.im);
+        dacc_fma(a.i0, x.re, y.im); dacc_fma(a.i1, x.im, y.re);
     }
     __device__ __forceinline__ static void fms(A& a, V x, V y) {
-        dacc_fma(a.re, df_neg(x.re), y.re); dacc_fma(a.re, x.im, y.im);
-        dacc_fma(a.im, df_neg(x.re), y.im); dacc_fma(a.im, df_neg(x.im), y.re);
+        dacc_fma(a.r0, df_neg(x.re), y.re); dacc_fma(a.r1, x.im, y.im);
+        dacc_fma(a.i0, df_neg(x.re), y.im); dacc_fma(a.i1, df_neg(x.im), y.re);
     }
-    __device__ __forceinline__ static void add(A& a, V x) { dacc_add(a.re, x.re); dacc_add(a.im, x.im); }
-    __device__ __forceinline__ static V get(const A& a) { V v; v.re = dacc_get(a.re); v.im = dacc_get(a.im); return v; }
+    __device__ __forceinline__ static void add(A& a, V x) { dacc_add(a.r0, x.re); dacc_add(a.i0, x.im); }
+    __device__ __forceinline__ static V get(const A& a) {
+        V v;
+        v.re = df_add(dacc_get(a.r0), dacc_get(a.r1));
+        v.im = df_add(dacc_get(a.i0), dacc_get(a.i1));
+        return v;
+    }
     __device__ __forceinline__ static V mul(V x, V y) {
         A a; acc_zero(a); fma(a, x, y); return get(a);
     }
@@ -170,7 +181,23 @@ struct MIXED {
     }
     __device__ __forceinline__ static cd to_cd(V x) { return cd_make(df_to_double(x.re), df_to_double(x.im)); }
     __device__ __forceinline__ static bool scaled() { return true; }
+    // Blocks are scaled to entries of order one; a pivot below 2^-64 is rounding residue
+    // of repeated rows or columns (a zero-determinant tuple), and inverting it could
+    // leave the FP32 exponent range, so the LU treats it as an exact zero.
+    __device__ __forceinline__ static float tiny() { return 0x1p-64f; }
 };
+
+// 16-byte read-only load of a precision-P value from global memory
+template <class V>
+__device__ __forceinline__ V ldv(const void* base, int64_t i) {
+    union { int4 raw; V v; } u;
+    u.raw = __ldg(reinterpret_cast<const int4*>(base) + i);
+    return u.v;
+}
+
+// conjugate
+__device__ __forceinline__ cd conj(cd x) { return cd_make(x.re, -x.im); }
+__device__ __forceinline__ cdf conj(cdf x) { cdf r = x; r.im = df_neg(x.im); return r; }
 
 // ------------------------------------------------------------------ double reductions
 // Compensated double accumulator (TwoSum of each addend, errors summed separately).

@@ -419,29 +419,26 @@ static void build_minor_plan(MinorPlan& mp, int n, const std::vector<Mask>& rows
 }
 
 // ------------------------------------------------------------------------ e-graph contraction
-static double egraph_cost(const HostPlan& p, int fa, const MinorPlan& A, const MinorPlan& B, int L, int n_j) {
-    (void)fa;
+static double egraph_cost(const HostPlan& p, int fa, const MinorPlan& A, const MinorPlan& B, int L,
+                          const std::vector<int>& used_j, const std::vector<int>& used_jp) {
     double cf = A.dp_cfma;
     int64_t nnz_s = 0;
-    for (auto& v : p.snk_can) nnz_s += (int64_t)v.size();
+    for (int j : used_j) nnz_s += (int64_t)p.snk_can[j].size();
     cf += (double)A.cols.size() * (double)nnz_s;                    // G_j per leaf
     // B cache build (levels <= L) once per site
     for (auto& nd : B.nodes) if (nd.level <= L) cf += (double)B.level_rows[nd.level].size() * nd.level;
     double path = 0;
     for (int k = L + 1; k <= B.n; ++k) path += (double)B.level_rows[k].size() * k;
-    int64_t n_pairs = 0;
-    {
-        // distinct (A column, B column) pairs over the used source indices
-        std::unordered_set<uint64_t> s;
-        for (auto& v : p.src_can)
-            for (auto& t : v) {
-                int64_t a = fa == 0 ? t.a : t.b, b = fa == 0 ? t.b : t.a;
-                s.insert(((uint64_t)a << 32) | (uint64_t)b);
-            }
-        n_pairs = (int64_t)s.size();
-    }
-    double nb = (double)(B.n ? B.level_rows[B.n].size() : 1);
-    cf += (double)n_pairs * (path + n_j * nb);
+    // distinct (A column, B column) pairs over the used source indices
+    std::unordered_set<uint64_t> s;
+    for (int jp : used_jp)
+        for (auto& t : p.src_can[jp]) {
+            int64_t a = fa == 0 ? t.a : t.b, b = fa == 0 ? t.b : t.a;
+            s.insert(((uint64_t)a << 32) | (uint64_t)b);
+        }
+    const double n_pairs = (double)s.size();
+    const double nb = (double)(B.n ? B.level_rows[B.n].size() : 1);
+    cf += n_pairs * (path + (used_j.size() + 1) * nb);              // B columns, then the weighted dots
     return cf;
 }
 
@@ -469,7 +466,7 @@ static void build_egraph(HostPlan& p, const std::vector<int>& used_j, const std:
         build_minor_plan(e.A, na, p.rows[fa], p.cols[fa]);
         build_minor_plan(e.B, nb, p.rows[1 - fa], p.cols[1 - fa]);
         e.cache_level = choose_cache_level(e.B);
-        double cost = egraph_cost(p, fa, e.A, e.B, e.cache_level, n_j);
+        double cost = egraph_cost(p, fa, e.A, e.B, e.cache_level, used_j, used_jp);
         if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = std::move(e); }
     }
     EgraphPlan& e = best;

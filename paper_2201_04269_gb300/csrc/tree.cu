@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) minor_table_kernel(TreeDev d, int flavour
         for (int i = 0; i < 6; ++i) {
             if (i < n) { rows[i] = d.minor_rows[flavour][mi * n + i]; cols[i] = d.minor_cols[flavour][mi * n + i]; }
         }
-        const V v = det_n<P>(n, sm + lane * kPad, rows, cols);
+        const V v = det_n<P, 12>(n, sm + lane * kPad, rows, cols);
         if (live) table[(table_off + mi) * wave + g0 + lane] = v;
     }
 }
@@ -100,9 +100,7 @@ __global__ void __launch_bounds__(256) tree_walk_kernel(TreeDev d, const typenam
         P::acc_zero(inner);
         for (int i = 0; i < nch; ++i) {
             const int32_t f2 = __ldg(d.factors + k + i);
-            const double2 cv = __ldg(reinterpret_cast<const double2*>(d.coefficients) + leaf + i);
-            const cd cf = cd_make(cv.x, cv.y);
-            P::fma(inner, P::from_cd(cf, 0), table[(int64_t)f2 * wave + col]);
+            P::fma(inner, ldv<V>(d.coefficients, leaf + i), table[(int64_t)f2 * wave + col]);
         }
         k += nch;
         leaf += nch;
