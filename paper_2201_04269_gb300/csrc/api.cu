@@ -167,21 +167,36 @@ mbc_status upload(mbc_plan* P) {
     size_t o_cn = b.add(h.tree.chunk_node), o_cl = b.add(h.tree.chunk_leaf), o_cc = b.add(h.tree.chunk_count);
     // e-graph
     EgraphPlan& e = h.eg;
-    struct MinorOffs { size_t child[7], row[7], lev, col, sign, leaf; } mo[2];
+    struct MinorOffs { size_t child[7], row[7], pack[7], lev, col, sign, leaf; } mo[2];
     const MinorPlan* mps[2] = {&e.A, &e.B};
     for (int w = 0; w < 2; ++w) {
         const MinorPlan& m = *mps[w];
-        for (int k = 0; k < 7; ++k) { mo[w].child[k] = b.add(m.child[k]); mo[w].row[k] = b.add(m.row[k]); }
+        for (int k = 0; k < 7; ++k) {
+            mo[w].child[k] = b.add(m.child[k]);
+            mo[w].row[k] = b.add(m.row[k]);
+            std::vector<uint32_t> pk(m.child[k].size());
+            for (size_t i = 0; i < pk.size(); ++i) pk[i] = (uint32_t)m.child[k][i] | ((uint32_t)m.row[k][i] << 16);
+            mo[w].pack[k] = b.add(pk);
+        }
         std::vector<uint8_t> lev, col;
         std::vector<int8_t> sg;
         std::vector<int32_t> leaf;
         for (auto& nd : m.nodes) { lev.push_back(nd.level); col.push_back(nd.col); sg.push_back(nd.sign); leaf.push_back(nd.leaf); }
         mo[w].lev = b.add(lev); mo[w].col = b.add(col); mo[w].sign = b.add(sg); mo[w].leaf = b.add(leaf);
     }
-    size_t o_cnodes = b.add(e.cache_nodes), o_cslot = b.add(e.cache_slot_of_node), o_bslot = b.add(e.bcol_slot);
-    size_t o_bpc = b.add(e.bcol_path_col), o_bps = b.add(e.bcol_path_sign);
-    size_t o_goff = b.add(e.g_off), o_gj = b.add(e.g_j), o_ga = b.add(e.g_a), o_gw = b.add(to_val(e.g_w, pr));
-    size_t o_poff = b.add(e.pair_off), o_pb = b.add(e.pair_b), o_pc = b.add(to_val(e.pair_coef, pr));
+    size_t o_goff = b.add(e.g_off), o_ga = b.add(e.g_a), o_gw = b.add(to_val(e.g_w, pr));
+    size_t o_poff = b.add(e.pair_off), o_pb = b.add(e.pair_b), o_pf = b.add(e.pair_first), o_pc = b.add(to_val(e.pair_coef, pr));
+    // compact form: real weights that a float holds exactly
+    bool compact = true;
+    for (auto& x : e.g_w) compact = compact && x.imag() == 0.0 && (double)(float)x.real() == x.real();
+    for (auto& x : e.pair_coef) compact = compact && x.imag() == 0.0 && (double)(float)x.real() == x.real();
+    std::vector<float> gwf, pcf;
+    std::vector<double> gwd, pcd;
+    if (compact) {
+        for (auto& x : e.g_w) { gwf.push_back((float)x.real()); gwd.push_back(x.real()); }
+        for (auto& x : e.pair_coef) { pcf.push_back((float)x.real()); pcd.push_back(x.real()); }
+    }
+    size_t o_gp = pr == 0 ? b.add(gwd) : b.add(gwf), o_pcf = pr == 0 ? b.add(pcd) : b.add(pcf);
 
     void* dev = nullptr;
     cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
@@ -215,38 +230,34 @@ mbc_status upload(mbc_plan* P) {
     EgraphDev& ed = P->ed;
     ed.flav_a = e.flav_a; ed.n_j = e.n_j;
     MinorDev* md[2] = {&ed.A, &ed.B};
-    int L = e.cache_level;
     for (int w = 0; w < 2; ++w) {
         const MinorPlan& m = *mps[w];
         MinorDev& x = *md[w];
         x.n = m.n;
-        minor_dev_offsets(m, w == 0 ? m.n : 6, x.size, x.off);
-        for (int k = 0; k < 7; ++k) { x.child[k] = at<uint16_t>(dev, mo[w].child[k]); x.row[k] = at<uint8_t>(dev, mo[w].row[k]); }
+        minor_dev_offsets(m, m.n, x.size, x.off);
+        for (int k = 0; k < 7; ++k) {
+            x.child[k] = at<uint16_t>(dev, mo[w].child[k]);
+            x.row[k] = at<uint8_t>(dev, mo[w].row[k]);
+            x.pack[k] = at<uint32_t>(dev, mo[w].pack[k]);
+        }
         x.n_nodes = (int)m.nodes.size();
         x.node_level = at<uint8_t>(dev, mo[w].lev); x.node_col = at<uint8_t>(dev, mo[w].col);
         x.node_sign = at<int8_t>(dev, mo[w].sign); x.node_leaf = at<int32_t>(dev, mo[w].leaf);
     }
-    ed.cache_level = L;
-    ed.n_cache_nodes = (int)e.cache_nodes.size();
-    ed.n_cache_slots = e.n_cache_slots;
-    ed.cache_nodes = at<int32_t>(dev, o_cnodes); ed.cache_slot = at<int32_t>(dev, o_cslot); ed.bcol_slot = at<int32_t>(dev, o_bslot);
-    ed.bcol_path_col = at<uint8_t>(dev, o_bpc); ed.bcol_path_sign = at<int8_t>(dev, o_bps);
+    ed.compact = compact ? 1 : 0;
+    ed.g_ws = at<unsigned char>(dev, o_gp);
+    ed.pair_cs = at<unsigned char>(dev, o_pcf);
+    ed.real_w = 1;
+    for (auto& x : e.g_w) if (x.imag() != 0.0) ed.real_w = 0;
+    for (auto& x : e.pair_coef) if (x.imag() != 0.0) ed.real_w = 0;
     ed.n_rows_b = e.B.n ? (int)e.B.level_rows[e.B.n].size() : 1;
-    ed.g_off = at<int32_t>(dev, o_goff); ed.g_j = at<int32_t>(dev, o_gj); ed.g_a = at<int32_t>(dev, o_ga); ed.g_w = at<Val16>(dev, o_gw);
-    ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_coef = at<Val16>(dev, o_pc);
+    ed.n_cols_b = e.B.n ? (int)e.B.cols.size() : 1;
+    ed.g_off = at<int32_t>(dev, o_goff); ed.g_a = at<int32_t>(dev, o_ga); ed.g_w = at<Val16>(dev, o_gw);
+    ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_first = at<uint8_t>(dev, o_pf);
+    ed.pair_coef = at<Val16>(dev, o_pc);
     ed.stack_a = ed.A.off[ed.A.n] + ed.A.size[ed.A.n];
-    ed.stack_b = e.B.n ? ed.B.off[L] : 0;
-    ed.path_b = 0;
-    for (int k = L + 1; k <= e.B.n; ++k) ed.path_b += ed.B.size[k];
-    int max_pairs = 1;
-    for (size_t i = 0; i + 1 < e.pair_off.size(); ++i) max_pairs = std::max(max_pairs, e.pair_off[i + 1] - e.pair_off[i]);
-    ed.n_batch = std::min(max_pairs, 4);
-    auto smem_values = [&](int nbatch) {
-        int fL = e.B.n ? ed.B.size[L] : 1;
-        return 2 * kBlk + ed.stack_a + ed.stack_b + ed.n_cache_slots * fL + nbatch * ed.path_b + ed.n_j * ed.n_rows_b;
-    };
-    while (ed.n_batch > 1 && smem_values(ed.n_batch) * 16 > 72 * 1024) --ed.n_batch;
-    ed.smem_values = smem_values(ed.n_batch);
+    ed.stack_b = ed.B.off[ed.B.n] + ed.B.size[ed.B.n];
+    ed.smem_values = 2 * kBlk + ed.stack_a + ed.stack_b + ed.n_j * ed.n_rows_b;
     return MBC_OK;
 }
 
@@ -291,6 +302,8 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
     if (it != ctx->tune_cache.end()) P->sched = it->second;
     else if (h.algo == MBC_ALGO_EGRAPH)   // as many blocks per SM as shared memory allows
         P->sched.blocks_per_sm = std::max(1, std::min(8, (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024))));
+    if (h.algo == MBC_ALGO_EGRAPH && P->sched.blocks_per_sm * (P->ed.smem_values * 16 + 3 * 1024) > 228 * 1024)
+        P->sched.blocks_per_sm = std::max(1, (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024)));
     ctx->plans.push_back(P);
     *out = P;
     ctx->err.clear();
@@ -348,8 +361,11 @@ mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int
         if (st != MBC_OK) return st;
         e = launch_tree(P->td, h.prec, u, d, g, c->scratch.p, wave, (int*)c->exps.p, parts, P->sched.threads, s, &c->launches);
     } else {
-        e = launch_egraph(P->ed, h.prec, u, d, g, parts, P->sched.threads, P->sched.blocks_per_sm,
-                          (unsigned int*)c->counter.p, s, &c->launches);
+        const int grid = (int)std::min<int64_t>(n_sites, (int64_t)c->sms * P->sched.blocks_per_sm);
+        st = ensure(c, c->scratch, egraph_kslot_bytes(P->ed) * (size_t)grid, s);
+        if (st != MBC_OK) return st;
+        e = launch_egraph(P->ed, h.prec, u, d, g, parts, P->sched.threads, grid, (unsigned int*)c->counter.p,
+                          c->scratch.p, s, &c->launches);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
     e = launch_reduce(parts, g, scale, (double2*)C, (double2*)site_out, (d4*)c->site_tmp.p, s, &c->launches);

@@ -69,6 +69,7 @@ struct MinorDev {
     int off[7];                    // offset of level k in a stacked table
     const uint16_t* child[7];      // [e * k + i]
     const uint8_t* row[7];
+    const uint32_t* pack[7];       // [e * k + i] = child | row << 16
     int n_nodes;
     const uint8_t* node_level;
     const uint8_t* node_col;
@@ -78,20 +79,17 @@ struct MinorDev {
 
 struct EgraphDev {
     int flav_a, n_j;
+    int real_w;                      // every G weight and pair coefficient is real
+    int compact;                     // ... and exact in float: g_ws / pair_cs hold them as
+    const void* g_ws;                // scalars of the precision (double or float): [entry]
+    const void* pair_cs;             // [pair * n_j + j]
     MinorDev A, B;
-    int cache_level, n_cache_nodes, n_cache_slots;
-    const int32_t* cache_nodes;      // B node ids (levels <= L) in DFS order
-    const int32_t* cache_slot;       // per cache node: slot or -1
-    const int32_t* bcol_slot;
-    const uint8_t* bcol_path_col;
-    const int8_t* bcol_path_sign;
-    int n_rows_b;
-    const int32_t* g_off; const int32_t* g_j; const int32_t* g_a; const void* g_w;   // g_w, pair_coef:
-    const int32_t* pair_off; const int32_t* pair_b; const void* pair_coef;           // precision-P values
+    int n_rows_b, n_cols_b;          // K is n_cols_b x n_rows_b per block slot
+    const int32_t* g_off; const int32_t* g_a; const void* g_w;           // g_w, pair_coef:
+    const int32_t* pair_off; const int32_t* pair_b; const uint8_t* pair_first;
+    const void* pair_coef;                                               // precision-P values
     int stack_a;                     // values in the A stack (levels 0..n_A)
-    int stack_b;                     // values in the B stack (levels 0..L-1)
-    int path_b;                      // values of one on-demand B column (levels L+1..n_B)
-    int n_batch;                     // B columns evaluated together
+    int stack_b;                     // values in the B stack (levels 0..n_B)
     int smem_values;                 // total complex values in dynamic shared memory
 };
 
@@ -103,9 +101,10 @@ cudaError_t launch_tree(const TreeDev& d, int prec, const double* U, const doubl
                         cudaStream_t s, int64_t* launches);
 size_t tree_value_bytes(int prec);
 cudaError_t launch_egraph(const EgraphDev& d, int prec, const double* U, const double* D, Geometry g,
-                          Partials out, int threads, int blocks_per_sm, unsigned int* counter,
+                          Partials out, int threads, int grid, unsigned int* counter, void* kscratch,
                           cudaStream_t s, int64_t* launches);
 size_t egraph_smem_bytes(const EgraphDev& d, int prec);
+size_t egraph_kslot_bytes(const EgraphDev& d);
 cudaError_t launch_reduce(Partials in, Geometry g, cd scale, double2* C, double2* site_out, d4* site_tmp,
                           cudaStream_t s, int64_t* launches);
 

@@ -76,6 +76,17 @@ __device__ __forceinline__ void dacc_fma(dacc& a, df x, df y) {
     a.hi = s;
     a.lo = __fadd_rn(a.lo, __fadd_rn(t, e));
 }
+// a += w * x with a float w (exact: w has no low part)
+__device__ __forceinline__ void dacc_fma_f(dacc& a, float w, df x) {
+    float p = __fmul_rn(x.hi, w);
+    float e = fmaf(x.hi, w, -p);
+    e = fmaf(x.lo, w, e);
+    float s = __fadd_rn(a.hi, p);
+    float bp = __fsub_rn(s, a.hi);
+    float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(t, e));
+}
 // a += x
 __device__ __forceinline__ void dacc_add(dacc& a, df x) {
     float s = __fadd_rn(a.hi, x.hi);
@@ -107,6 +118,16 @@ struct FP64 {
         a.im = __fma_rn(-x.re, y.im, a.im); a.im = __fma_rn(-x.im, y.re, a.im);
     }
     __device__ __forceinline__ static void add(A& a, V x) { a.re += x.re; a.im += x.im; }
+    // a += w * x for a real w (the real part of a precision-P value)
+    __device__ __forceinline__ static void fma_real(A& a, V w, V x) {
+        a.re = __fma_rn(w.re, x.re, a.re); a.im = __fma_rn(w.re, x.im, a.im);
+    }
+    // a += w * x for a real scalar weight
+    typedef double S;
+    __device__ __forceinline__ static void fma_s(A& a, S w, V x) {
+        a.re = __fma_rn(w, x.re, a.re); a.im = __fma_rn(w, x.im, a.im);
+    }
+    __device__ __forceinline__ static V vadd(V a, V b) { return cd_make(a.re + b.re, a.im + b.im); }
     __device__ __forceinline__ static V get(const A& a) { return a; }
     __device__ __forceinline__ static V mul(V x, V y) {
         return cd_make(__fma_rn(x.re, y.re, -x.im * y.im), __fma_rn(x.re, y.im, x.im * y.re));
@@ -148,6 +169,12 @@ struct MIXED {
         dacc_fma(a.i0, df_neg(x.re), y.im); dacc_fma(a.i1, df_neg(x.im), y.re);
     }
     __device__ __forceinline__ static void add(A& a, V x) { dacc_add(a.r0, x.re); dacc_add(a.i0, x.im); }
+    // a += w * x for a real w (the real part of a precision-P value)
+    __device__ __forceinline__ static void fma_real(A& a, V w, V x) { dacc_fma(a.r0, w.re, x.re); dacc_fma(a.i0, w.re, x.im); }
+    // a += w * x for a real scalar weight held exactly in a float
+    typedef float S;
+    __device__ __forceinline__ static void fma_s(A& a, S w, V x) { dacc_fma_f(a.r0, w, x.re); dacc_fma_f(a.i0, w, x.im); }
+    __device__ __forceinline__ static V vadd(V a, V b) { V r; r.re = df_add(a.re, b.re); r.im = df_add(a.im, b.im); return r; }
     __device__ __forceinline__ static V get(const A& a) {
         V v;
         v.re = df_add(dacc_get(a.r0), dacc_get(a.r1));

@@ -41,24 +41,18 @@ struct MinorPlan {
 };
 
 struct EgraphPlan {
-    int flav_a = 0;                             // flavour streamed by the column tree (0 = u)
+    int flav_a = 0;                             // flavour streamed first (0 = u)
     int n_j = 0;                                // sink free indices in use
     MinorPlan A, B;
-    int cache_level = 1;                        // B tables kept per level-L column prefix
-    std::vector<int32_t> cache_nodes;           // B tree nodes (depth <= L) in DFS order
-    std::vector<int32_t> cache_slot_of_node;    // slot of a level-L node, else -1
-    int n_cache_slots = 0;
-    // per needed B column: cache slot of its level-L ancestor, and the path below it
-    std::vector<int32_t> bcol_slot;
-    std::vector<uint8_t> bcol_path_col;         // [col * (n_B - L) + s]
-    std::vector<int8_t> bcol_path_sign;
-    // G_j(b) = sum over entries (j, a, w) of w * A(a); entries grouped by b
-    std::vector<int32_t> g_off;                 // [|rows_B| + 1]
-    std::vector<int32_t> g_j, g_a;
+    // G_j(b) = sum over entries (a, w) of w * A(a); entries grouped by (b, j)
+    std::vector<int32_t> g_off;                 // [|rows_B| * n_j + 1]
+    std::vector<int32_t> g_a;
     std::vector<cplx> g_w;
-    // per A leaf (needed A column): pairs (B column, coef_j for each j)
+    // per A leaf (needed A column): pairs (B column, coef_j for each j); a pair is the
+    // first update of its B column in traversal order when pair_first is 1
     std::vector<int32_t> pair_off;              // [|cols_A| + 1]
     std::vector<int32_t> pair_b;
+    std::vector<uint8_t> pair_first;
     std::vector<cplx> pair_coef;                // [pair * n_j + j]
     double flops_per_site = 0;
 };

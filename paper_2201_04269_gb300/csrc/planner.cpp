@@ -419,38 +419,27 @@ static void build_minor_plan(MinorPlan& mp, int n, const std::vector<Mask>& rows
 }
 
 // ------------------------------------------------------------------------ e-graph contraction
-static double egraph_cost(const HostPlan& p, int fa, const MinorPlan& A, const MinorPlan& B, int L,
-                          const std::vector<int>& used_j, const std::vector<int>& used_jp) {
-    double cf = A.dp_cfma;
+static double egraph_cost(const HostPlan& p, int fa, const MinorPlan& A, const MinorPlan& B,
+                          const std::vector<int>& used_j, const std::vector<int>& used_jp, double weight_factor = 1.0) {
+    // complex multiply-adds per site of the staged evaluation:
+    //   A column tree, G_j per A leaf, K(:, C_b) += sum_j coef_j G_j per pair,
+    //   B column tree, <K(:, C_b), det B[:, C_b]> per B leaf
+    double cf = A.dp_cfma + B.dp_cfma;
     int64_t nnz_s = 0;
     for (int j : used_j) nnz_s += (int64_t)p.snk_can[j].size();
-    cf += (double)A.cols.size() * (double)nnz_s;                    // G_j per leaf
-    // B cache build (levels <= L) once per site
-    for (auto& nd : B.nodes) if (nd.level <= L) cf += (double)B.level_rows[nd.level].size() * nd.level;
-    double path = 0;
-    for (int k = L + 1; k <= B.n; ++k) path += (double)B.level_rows[k].size() * k;
-    // distinct (A column, B column) pairs over the used source indices
+    // real weights multiply a complex value with two real multiply-adds (factor 1/2)
+    cf += weight_factor * (double)A.cols.size() * (double)nnz_s;
     std::unordered_set<uint64_t> s;
     for (int jp : used_jp)
         for (auto& t : p.src_can[jp]) {
             int64_t a = fa == 0 ? t.a : t.b, b = fa == 0 ? t.b : t.a;
             s.insert(((uint64_t)a << 32) | (uint64_t)b);
         }
-    const double n_pairs = (double)s.size();
     const double nb = (double)(B.n ? B.level_rows[B.n].size() : 1);
-    cf += n_pairs * (path + (used_j.size() + 1) * nb);              // B columns, then the weighted dots
+    const double ncb = (double)(B.n ? B.cols.size() : 1);
+    cf += weight_factor * (double)s.size() * nb * (double)used_j.size();
+    cf += ncb * nb;
     return cf;
-}
-
-static int choose_cache_level(const MinorPlan& B) {
-    if (B.n <= 1) return B.n;
-    int best = 1;
-    for (int L = 1; L <= B.n - 1; ++L) {
-        int64_t slots = 0;
-        for (auto& nd : B.nodes) if (nd.level == L) ++slots;
-        if (slots * (int64_t)B.level_rows[L].size() * 16 <= 48 * 1024) best = L;
-    }
-    return best;
 }
 
 static void build_egraph(HostPlan& p, const std::vector<int>& used_j, const std::vector<int>& used_jp) {
@@ -465,41 +454,13 @@ static void build_egraph(HostPlan& p, const std::vector<int>& used_j, const std:
         e.n_j = n_j;
         build_minor_plan(e.A, na, p.rows[fa], p.cols[fa]);
         build_minor_plan(e.B, nb, p.rows[1 - fa], p.cols[1 - fa]);
-        e.cache_level = choose_cache_level(e.B);
-        double cost = egraph_cost(p, fa, e.A, e.B, e.cache_level, used_j, used_jp);
+        // K holds |cols_B| x |rows_B| values: prefer the smaller second flavour
+        double cost = egraph_cost(p, fa, e.A, e.B, used_j, used_jp);
         if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = std::move(e); }
     }
     EgraphPlan& e = best;
     const int fa = e.flav_a;
-    const int nB = e.B.n, L = e.cache_level;
-    // B cache: tree nodes of depth <= L in depth-first order, slots for level-L nodes
-    e.n_cache_slots = 0;
-    std::vector<int32_t> slot_of(e.B.nodes.size(), -1);
-    for (size_t i = 0; i < e.B.nodes.size(); ++i) {
-        if (e.B.nodes[i].level > L) continue;
-        e.cache_nodes.push_back((int32_t)i);
-        if (e.B.nodes[i].level == L) slot_of[i] = e.n_cache_slots++;
-        e.cache_slot_of_node.push_back(slot_of[i]);
-    }
-    // every needed B column: its level-L ancestor and the path below it
-    const size_t nbc = nB ? e.B.cols.size() : 1;
-    e.bcol_slot.assign(nbc, 0);
-    e.bcol_path_col.assign(nbc * (size_t)std::max(nB - L, 0), 0);
-    e.bcol_path_sign.assign(nbc * (size_t)std::max(nB - L, 0), 1);
-    if (nB) {
-        for (size_t i = 0; i < e.B.nodes.size(); ++i) {
-            const auto& nd = e.B.nodes[i];
-            if (nd.level != nB) continue;
-            std::vector<int32_t> chain;
-            for (int32_t v = (int32_t)i; v >= 0; v = e.B.nodes[v].parent) chain.push_back(v);
-            std::reverse(chain.begin(), chain.end());   // levels 1..nB
-            e.bcol_slot[nd.leaf] = slot_of[chain[L - 1]];
-            for (int k = L + 1; k <= nB; ++k) {
-                e.bcol_path_col[(size_t)nd.leaf * (nB - L) + (k - L - 1)] = e.B.nodes[chain[k - 1]].col;
-                e.bcol_path_sign[(size_t)nd.leaf * (nB - L) + (k - L - 1)] = e.B.nodes[chain[k - 1]].sign;
-            }
-        }
-    }
+    const int nB = e.B.n;
     // G entries grouped by (B row set, j): (A row set, w)
     const size_t n_rb = nB ? p.rows[1 - fa].size() : 1;
     std::vector<std::vector<std::pair<int32_t, cplx>>> byb(n_rb * (size_t)n_j);
@@ -510,7 +471,7 @@ static void build_egraph(HostPlan& p, const std::vector<int>& used_j, const std:
         }
     e.g_off.assign(1, 0);
     for (auto& v : byb) {
-        for (auto& x : v) { e.g_j.push_back(0); e.g_a.push_back(x.first); e.g_w.push_back(x.second); }
+        for (auto& x : v) { e.g_a.push_back(x.first); e.g_w.push_back(x.second); }
         e.g_off.push_back((int32_t)e.g_a.size());
     }
     // pairs per A column: coef_j = sum_j' P_jj' conj(r_j'(C_a, C_b))
@@ -524,14 +485,32 @@ static void build_egraph(HostPlan& p, const std::vector<int>& used_j, const std:
             for (int jj = 0; jj < n_j; ++jj) coef[jj] += p.proj[(size_t)used_j[jj] * p.n_free + jp] * std::conj(t.w);
         }
     e.pair_off.assign(1, 0);
-    for (auto& m : pairs) {
-        for (auto& kv : m) {
+    std::vector<char> seen(nB ? p.cols[1 - fa].size() : 1, 0);
+    // leaves are visited in column-tree order: first touches follow that order
+    std::vector<int32_t> leaf_order;
+    for (auto& nd : e.A.nodes) if (nd.leaf >= 0) leaf_order.push_back(nd.leaf);
+    std::vector<int32_t> first_of_leaf(n_ca, 0);
+    std::vector<std::vector<uint8_t>> first(n_ca);
+    for (int32_t leaf : leaf_order) {
+        for (auto& kv : pairs[leaf]) {
+            first[leaf].push_back(seen[kv.first] ? 0 : 1);
+            seen[kv.first] = 1;
+        }
+    }
+    for (size_t ca = 0; ca < n_ca; ++ca) {
+        size_t i = 0;
+        for (auto& kv : pairs[ca]) {
             e.pair_b.push_back(kv.first);
+            e.pair_first.push_back(first[ca].empty() ? 0 : first[ca][i]);
             for (int jj = 0; jj < n_j; ++jj) e.pair_coef.push_back(kv.second[jj]);
+            ++i;
         }
         e.pair_off.push_back((int32_t)e.pair_b.size());
     }
-    e.flops_per_site = 8.0 * best_cost;
+    bool real = true;
+    for (auto& x : e.g_w) real = real && x.imag() == 0.0;
+    for (auto& x : e.pair_coef) real = real && x.imag() == 0.0;
+    e.flops_per_site = 8.0 * egraph_cost(p, fa, e.A, e.B, used_j, used_jp, real ? 0.5 : 1.0);
     p.eg = std::move(e);
     p.flops_egraph = p.eg.flops_per_site;
 }
@@ -710,7 +689,7 @@ std::string plan_explicit(HostPlan& p) {
 
 // ------------------------------------------------------------------------ serialisation
 namespace {
-const char kMagic[8] = {'M', 'B', 'C', 'P', 'L', 'A', 'N', '1'};
+const char kMagic[8] = {'M', 'B', 'C', 'P', 'L', 'A', 'N', '2'};
 struct W {
     FILE* f;
     bool ok = true;
@@ -747,10 +726,9 @@ template <class S> void plan_io(S& s, HostPlan& p) {
     s.vec(t.factors); s.vec(t.children); s.vec(t.coefficients); s.pod(t.n_level1);
     s.vec(t.chunk_node); s.vec(t.chunk_leaf); s.vec(t.chunk_count);
     EgraphPlan& e = p.eg;
-    s.pod(e.flav_a); s.pod(e.n_j); minor_io(s, e.A); minor_io(s, e.B); s.pod(e.cache_level);
-    s.vec(e.cache_nodes); s.vec(e.cache_slot_of_node); s.pod(e.n_cache_slots); s.vec(e.bcol_slot);
-    s.vec(e.bcol_path_col); s.vec(e.bcol_path_sign); s.vec(e.g_off); s.vec(e.g_j); s.vec(e.g_a); s.vec(e.g_w);
-    s.vec(e.pair_off); s.vec(e.pair_b); s.vec(e.pair_coef); s.pod(e.flops_per_site);
+    s.pod(e.flav_a); s.pod(e.n_j); minor_io(s, e.A); minor_io(s, e.B);
+    s.vec(e.g_off); s.vec(e.g_a); s.vec(e.g_w);
+    s.vec(e.pair_off); s.vec(e.pair_b); s.vec(e.pair_first); s.vec(e.pair_coef); s.pod(e.flops_per_site);
     DirectPlan& d = p.direct;
     s.vec(d.blk_s0); s.vec(d.blk_s1); s.vec(d.blk_r0); s.vec(d.blk_r1); s.vec(d.blk_p); s.pod(d.index_size);
     s.pod(p.flops_direct); s.pod(p.flops_tree); s.pod(p.flops_egraph);

@@ -286,3 +286,35 @@ def test_autotune_keeps_results(ctx):
     C2, _ = run(plan, U[None], D[None])
     check(C2, C1, "mixed")
     plan.destroy()
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_random_complex_factored(ctx, algo, prec):
+    """A random factored problem (n_u = 3, n_d = 2, two free indices, complex weights,
+    a complex projector, sink and source patterns that differ) against the oracle's
+    index-set sum: exercises the general complex-weight paths."""
+    rng = np.random.default_rng(33)
+    from paper_2201_04269_gb300 import abi
+
+    def side(n):
+        idx = rng.integers(0, 12, size=(n, 5)).astype(np.int8)
+        w = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        return idx, w
+    si, sw = side(60)
+    ri, rw = side(50)
+    soff = np.array([0, 25, 60])
+    roff = np.array([0, 30, 50])
+    P = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    scale = 0.5 - 0.25j
+    h = abi.mbc_plan_create(ctx.handle, 3, 2, si, sw, soff, ri, rw, roff, P, scale, algo, prec)
+    from paper_2201_04269_gb300 import Plan
+    plan = Plan(ctx, h)
+    U, D = mi.workload_fields("proton_4x8", L=2, T=2)
+    C, S = run(plan, U[None], D[None])
+    snk = [(si[soff[j]:soff[j + 1]], sw[soff[j]:soff[j + 1]]) for j in range(2)]
+    src = [(ri[roff[j]:roff[j + 1]], rw[roff[j]:roff[j + 1]]) for j in range(2)]
+    # the oracle applies the Wick sign of n = 5 (+1); the plan multiplies by `scale`
+    ref = scale * onat.direct(3, 2, snk, src, P, U.reshape(-1, 12, 12), D.reshape(-1, 12, 12))
+    check(S[0].ravel(), ref, prec)
+    plan.destroy()
