@@ -214,6 +214,34 @@ mbc_status mbc_autotune(mbc_plan* plan, const void* U, const void* D, int64_t n_
 mbc_status mbc_set_schedule(mbc_plan* plan, const mbc_schedule* s);
 mbc_status mbc_get_schedule(const mbc_plan* plan, mbc_schedule* s);
 
+/* ------------------------------------------------------------------------------------
+ * Evaluation without device allocation.  The paper has no counterpart to this entry
+ * point; it serves callers that may not allocate device memory at the moment they
+ * evaluate: code running while a stream is captured into a CUDA graph, services whose
+ * device memory budget is fixed up front, hosts that forbid allocation after start up.
+ *
+ * mbc_correlator_noalloc computes exactly what mbc_correlator computes (C only, no
+ * per-site output) for an MBC_ALGO_EGRAPH plan, with every temporary (work counter,
+ * per-site partial sums, the kernel's K slots) taken from one fixed device array of
+ * MBC_NOALLOC_SCRATCH_BYTES bytes built into the library; it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The caller still supplies the fields U, D
+ * and the output C (device memory, same layouts as mbc_correlator); the plan must
+ * have been created beforehand (plan creation allocates).
+ *  - Every GPU that loads this part of the library holds the array until the process
+ *    exits.  The first call on a device looks up the array's device address; make that
+ *    first call before any stream capture that is to include later calls.
+ *  - All calls share the array and it keeps the last call's contents (the work counter
+ *    is cleared on the stream at each call; nothing else needs to start at zero).
+ *    Calls whose device work overlaps (different streams, or different host threads on
+ *    one device) race on the array: serialise them on one stream.
+ *  - A call needing more than the array holds (32 bytes per sink site plus one K slot
+ *    of the plan, |cols_B| x |rows_B| x 16 bytes, plus 256) returns MBC_UNSUPPORTED
+ *    and a message giving the sizes; fewer K slots than blocks reduce the grid instead.
+ * ---------------------------------------------------------------------------------- */
+#define MBC_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, const void* D, int n_sets, int T, int64_t V3,
+                                  void* C, mbc_stream stream);
+
 /* Number of device kernel launches made by this context since it was created (every
  * launch of every mbc call counts once). */
 int64_t mbc_launch_count(const mbc_ctx* ctx);

@@ -89,6 +89,7 @@ SIGNATURES = [
     ("mbc_set_schedule", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_schedule)]),
     ("mbc_get_schedule", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_schedule)]),
     ("mbc_launch_count", ctypes.c_int64, [c_vp]),
+    ("mbc_correlator_noalloc", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, c_vp, c_vp]),
 ]
 
 _LIB = None
@@ -265,6 +266,11 @@ def mbc_plan_load(ctx, path):
 
 def mbc_correlator(plan, U, D, n_sets, T, V3, C, site_out=None, stream=None, ctx=None):
     check(load().mbc_correlator(plan, dptr(U), dptr(D), n_sets, T, V3, dptr(C), dptr(site_out), sptr(stream)), ctx)
+
+
+def mbc_correlator_noalloc(plan, U, D, n_sets, T, V3, C, stream=None, ctx=None):
+    """mbc_correlator without device allocation (fixed scratch array in the library)."""
+    check(load().mbc_correlator_noalloc(plan, dptr(U), dptr(D), n_sets, T, V3, dptr(C), sptr(stream)), ctx)
 
 
 def mbc_correlator_host(plan, U_host, D_host, n_sets, T, V3, C_host, stream=None, ctx=None):

@@ -11,6 +11,7 @@
 #include "mbc.h"
 #include "device.cuh"
 #include "plan.hpp"
+#include "noalloc.hpp"
 
 using namespace mbc;
 
@@ -376,6 +377,25 @@ mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int
 bool bad_ptr(const void* p) { return p == nullptr; }
 
 }  // namespace
+
+namespace mbc {
+// Read-only view of a plan for the allocation-free entry point (noalloc.cu).
+bool noalloc_view(mbc_plan* P, NoallocView* v) {
+    if (!P || !P->ctx) return false;
+    v->device = P->ctx->device;
+    v->algo = P->hp.algo;
+    v->prec = P->hp.prec;
+    v->threads = P->sched.threads;
+    v->blocks_per_sm = P->sched.blocks_per_sm;
+    v->sms = P->ctx->sms;
+    v->scale = cd_make(P->hp.scale.real(), P->hp.scale.imag());
+    v->ed = P->ed;
+    v->empty = P->hp.terms.empty();
+    v->err = &P->ctx->err;
+    v->launches = &P->ctx->launches;
+    return true;
+}
+}  // namespace mbc
 
 // ====================================================================== C ABI
 extern "C" {
