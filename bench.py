@@ -50,6 +50,37 @@ def fp32_peak_tflops(sm_mhz):
     return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
+KERNEL_SOURCES = ("egraph.cu", "numeric.cuh", "common.cuh", "device.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "egraph_kernel_he3_II_s_24x48.md")
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2201_04269_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic_per_site():
+    """DRAM bytes per site from the committed ncu summary, if the kernel sources are
+    unchanged since it was taken (else None)."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("kernel_source_hash:"):
+            vals["hash"] = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_site:"):
+            vals["bytes"] = float(line.split(":", 1)[1].strip())
+    if vals.get("hash") != kernel_hash() or "bytes" not in vals:
+        return None
+    return vals["bytes"]
+
+
 def fields(set_index, t_list=None):
     import mbc_inputs as mi
     U = mi.propagator_field(SEED, set_index, 0, T, L ** 3, KAPPA, None, t_list)
@@ -229,8 +260,10 @@ def main():
     flops = info["flops_per_site"] * n_sites
     achieved = flops / (ms * 1e-3) / 1e12
     peak = fp32_peak_tflops(sm_max)
+    tps = recorded_traffic_per_site()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "egraph_kernel<MIXED>",
+                "traffic": None if tps is None else tps * n_sites, "kernel": "egraph_kernel<MIXED>",
+                "kernel_source_hash": kernel_hash(),
                 "flops_per_site": info["flops_per_site"], "flop_model": "8 flop per complex multiply-add of the plan",
                 "peak_basis": f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz (derived)"}
 

@@ -256,9 +256,11 @@ mbc_status upload(mbc_plan* P) {
     ed.g_off = at<int32_t>(dev, o_goff); ed.g_a = at<int32_t>(dev, o_ga); ed.g_w = at<Val16>(dev, o_gw);
     ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_first = at<uint8_t>(dev, o_pf);
     ed.pair_coef = at<Val16>(dev, o_pc);
-    ed.stack_a = ed.A.off[ed.A.n] + ed.A.size[ed.A.n];
-    ed.stack_b = ed.B.off[ed.B.n] + ed.B.size[ed.B.n];
-    ed.smem_values = 2 * kBlk + ed.stack_a + ed.stack_b + ed.n_j * ed.n_rows_b;
+    // levels 0..n-1 plus two buffers for the leaf level; G only for the general leaf path
+    ed.stack_a = ed.A.off[ed.A.n] + 2 * ed.A.size[ed.A.n];
+    ed.stack_b = ed.B.off[ed.B.n] + 2 * ed.B.size[ed.B.n];
+    const bool fused = compact && ed.n_j <= 2;
+    ed.smem_values = 2 * kBlk + ed.stack_a + ed.stack_b + (fused ? 0 : ed.n_j * ed.n_rows_b);
     return MBC_OK;
 }
 
@@ -301,10 +303,13 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
     P->signature = signature(h);
     auto it = ctx->tune_cache.find(P->signature);
     if (it != ctx->tune_cache.end()) P->sched = it->second;
-    else if (h.algo == MBC_ALGO_EGRAPH)   // as many blocks per SM as shared memory allows
-        P->sched.blocks_per_sm = std::max(1, std::min(8, (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024))));
-    if (h.algo == MBC_ALGO_EGRAPH && P->sched.blocks_per_sm * (P->ed.smem_values * 16 + 3 * 1024) > 228 * 1024)
-        P->sched.blocks_per_sm = std::max(1, (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024)));
+    else if (h.algo == MBC_ALGO_EGRAPH) {
+        // 384 threads (12 warps) per block, as many blocks per SM as shared memory and
+        // the 2048-thread limit allow
+        P->sched.threads = 384;
+        const int by_smem = (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024));
+        P->sched.blocks_per_sm = std::max(1, std::min(by_smem, 2048 / P->sched.threads));
+    }
     ctx->plans.push_back(P);
     *out = P;
     ctx->err.clear();
@@ -686,8 +691,11 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
 
 mbc_status mbc_set_schedule(mbc_plan* P, const mbc_schedule* s) {
     if (!P || !s) return MBC_INVALID_ARG;
-    if (s->threads < 32 || s->threads > 256 || s->threads % 32 || s->blocks_per_sm < 1 || s->blocks_per_sm > 32 || s->sites_per_unit < 1)
-        return fail(P->ctx, MBC_INVALID_ARG, "schedule out of range (threads 32..256, multiple of 32)");
+    const int max_threads = P->hp.algo == MBC_ALGO_EGRAPH ? 384 : 256;
+    if (s->threads < 32 || s->threads > max_threads || s->threads % 32 || s->blocks_per_sm < 1 || s->blocks_per_sm > 32 ||
+        s->sites_per_unit < 1)
+        return fail(P->ctx, MBC_INVALID_ARG, "schedule out of range (threads 32..256, or ..384 for the e-graph kernels, "
+                                             "a multiple of 32)");
     P->sched = *s;
     return MBC_OK;
 }
@@ -706,8 +714,10 @@ mbc_status mbc_autotune(mbc_plan* P, const void* U, const void* D, int64_t n_sit
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<mbc_schedule> cands;
     const int smem = P->ed.smem_values * 16 + 1024;
-    for (int th : {128, 256})
+    for (int th : {128, 256, 320, 384})
         for (int bps : {1, 2, 3, 4, 6, 8}) {
+            if (th > 256 && P->hp.algo != MBC_ALGO_EGRAPH) continue;
+            if (th * bps > 2048) continue;
             if (P->hp.algo == MBC_ALGO_EGRAPH && bps * smem > 220 * 1024) continue;
             if (P->hp.algo != MBC_ALGO_EGRAPH && bps != 2) continue;
             for (int spu : {1, 4}) {

@@ -97,12 +97,14 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
 }
 
 template <class P>
-__global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* __restrict__ U,
+__global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* __restrict__ U,
                                                      const double* __restrict__ D, Geometry g, Partials out,
                                                      unsigned int* __restrict__ counter,
                                                      typename P::V* __restrict__ kscratch) {
     typedef typename P::V V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // shared memory: the two staged blocks, the A stack (levels 0..nA-1 and two buffers
+    // for the leaf level), the B stack (likewise), and G for the general leaf path
     V* sA = reinterpret_cast<V*>(smem_raw);
     V* sB = sA + kBlk;
     V* stA = sB + kBlk;
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
     __shared__ unsigned int s_unit;
     const int nA = d.A.n, nB = d.B.n;
     const int n_rb = d.n_rows_b, nj = d.n_j;
+    const bool fused = d.compact && nj <= 2;
     V* K = kscratch + (size_t)blockIdx.x * d.n_cols_b * n_rb;      // this block's K slot
     const int64_t n_units = g.n_sites();
     for (;;) {
@@ -130,18 +133,24 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
         }
         __syncthreads();
         // ---- phase 1: A column tree, G_j per leaf, K updates per pair
+        int parity = 0;
         for (int nd = 0; nd < d.A.n_nodes; ++nd) {
             const int k = __ldg(d.A.node_level + nd);
+            // leaf-level tables alternate between two buffers, so the next leaf's Laplace
+            // step may start while slower threads still read this leaf's table
+            V* dest = stA + d.A.off[k] + (k == nA ? parity * d.A.size[nA] : 0);
             laplace_level<P>(d.A, k, __ldg(d.A.node_col + nd), __ldg(d.A.node_sign + nd), sA, stA + d.A.off[k - 1],
-                             stA + d.A.off[k]);
+                             dest);
             __syncthreads();
             const int leaf = __ldg(d.A.node_leaf + nd);
             if (leaf < 0) continue;
-            const V* T = stA + d.A.off[nA];
-            if (d.compact && nj <= 2) {
+            const V* T = dest;
+            parity ^= 1;
+            if (fused) {
                 if (nj == 1) leaf_fused<P, 1>(d, leaf, T, K);
                 else leaf_fused<P, 2>(d, leaf, T, K);
-                __syncthreads();     // T (the A table of this leaf) is rewritten by the next leaf
+                // no barrier: the next leaf writes the other buffer, and the barrier after
+                // the next Laplace step orders these K writes before later K updates
                 continue;
             }
             {   // G_j(R_b) = sum_{R_a} s_j(R_a, R_b) T(R_a); flat index it = b * nj + j
@@ -185,8 +194,8 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
                     if (b >= n_rb) { b -= n_rb; ++bi; }
                 }
             }
-            // the next A node's level step writes only the A stack; its barrier orders
-            // these K writes before any later read or update of the same K column
+            // G is rewritten by the next leaf only after the barrier that follows the next
+            // Laplace step, which also orders these K writes before later K updates
         }
         __syncthreads();
         // ---- phase 2: B column tree, <K(C_b, :), det B[:, C_b]> per leaf
@@ -195,17 +204,18 @@ __global__ void __launch_bounds__(256) egraph_kernel(EgraphDev d, const double* 
         if (nB == 0) {
             if (threadIdx.x == 0) P::add(acc, K[0]);
         } else {
+            int pb = 0;
             for (int nd = 0; nd < d.B.n_nodes; ++nd) {
                 const int k = __ldg(d.B.node_level + nd);
+                V* dest = stB + d.B.off[k] + (k == nB ? pb * d.B.size[nB] : 0);
                 laplace_level<P>(d.B, k, __ldg(d.B.node_col + nd), __ldg(d.B.node_sign + nd), sB, stB + d.B.off[k - 1],
-                                 stB + d.B.off[k]);
+                                 dest);
                 __syncthreads();
                 const int leaf = __ldg(d.B.node_leaf + nd);
                 if (leaf < 0) continue;
-                const V* T = stB + d.B.off[nB];
+                pb ^= 1;
                 const V* kc = K + (size_t)leaf * n_rb;
-                for (int b = threadIdx.x; b < n_rb; b += blockDim.x) P::fma(acc, kc[b], T[b]);
-                __syncthreads();
+                for (int b = threadIdx.x; b < n_rb; b += blockDim.x) P::fma(acc, kc[b], dest[b]);
             }
         }
         // ---- site value
