@@ -185,11 +185,15 @@ mbc_status mbc_correlator(mbc_plan* plan, const void* U, const void* D, int n_se
 mbc_status mbc_correlator_host(mbc_plan* plan, const void* U_host, const void* D_host, int n_sets, int T,
                                int64_t V3, void* C_host, mbc_stream stream);
 
-/* Batched evaluation: several (plan, fields, output) items in one persistent launch per
- * kernel family, load-balanced over (item, set, t, site block) work units by an atomic
- * counter (no inter-block waiting).  Items must use plans of this context; an item's
- * algorithm must be MBC_ALGO_EGRAPH (the batched scheduler runs the e-graph kernels).
- * Capturable in a CUDA graph once mbc_batch_reserve has sized the pool for the items. */
+/* Batched evaluation: several (plan, fields, output) items -- different operators,
+ * propagator sets and lattice sizes -- in one persistent launch per precision, load
+ * balanced over (item, site) work units by an atomic counter (no inter-block waiting),
+ * followed by one small site-sum launch per item.  Items must use MBC_ALGO_EGRAPH plans
+ * of this context.  mbc_batch_reserve sizes the device buffers and uploads the item
+ * table (synchronously); mbc_batch with the same item array (same plans, pointers and
+ * sizes) then allocates nothing and can be captured in a CUDA graph.  Called with other
+ * items outside a capture, mbc_batch reserves them first; inside a capture it fails
+ * with MBC_OOM. */
 typedef struct {
     mbc_plan* plan;
     const void* U;

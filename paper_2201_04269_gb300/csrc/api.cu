@@ -33,8 +33,13 @@ struct mbc_ctx {
     Buf partials, site_tmp, scratch, exps, counter, hU, hD, hC;
     std::vector<mbc_plan*> plans;
     std::map<std::string, mbc_schedule> tune_cache;
-    // batched launches
-    Buf batch_items, batch_parts;
+    // batched launches: item tables per precision (device) and the reserved item list
+    Buf batch_items, batch_parts, batch_k;
+    std::vector<mbc_work> batch_reserved;
+    std::vector<BatchItem> batch_host[2];
+    size_t batch_smem[2] = {0, 0};
+    int64_t batch_units[2] = {0, 0}, batch_kslot = 0;
+    int batch_grid = 0;
 };
 
 struct mbc_plan {
@@ -442,7 +447,7 @@ void mbc_destroy(mbc_ctx* c) {
     cudaDeviceSynchronize();
     for (mbc_plan* p : c->plans) { if (p->dev) cudaFree(p->dev); delete p; }
     Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
-                   &c->batch_items, &c->batch_parts};
+                   &c->batch_items, &c->batch_parts, &c->batch_k};
     for (Buf* b : bufs) if (b->p) cudaFree(b->p);
     delete c;
 }
@@ -663,29 +668,126 @@ mbc_status mbc_correlator_host(mbc_plan* P, const void* U_host, const void* D_ho
     return MBC_OK;
 }
 
-mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
-    if (!c || (n_items && !items) || n_items < 0) return c ? fail(c, MBC_INVALID_ARG, "bad items") : MBC_INVALID_ARG;
+namespace {
+bool same_items(const std::vector<mbc_work>& a, const mbc_work* b, int n) {
+    if ((int)a.size() != n) return false;
+    for (int i = 0; i < n; ++i)
+        if (std::memcmp(&a[i], &b[i], sizeof(mbc_work)) != 0) return false;
+    return true;
+}
+
+mbc_status check_items(mbc_ctx* c, const mbc_work* items, int n_items) {
+    if (n_items < 0 || (n_items && !items)) return fail(c, MBC_INVALID_ARG, "bad items");
     if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
-    int64_t sites = 0;
-    for (int i = 0; i < n_items; ++i) sites = std::max<int64_t>(sites, (int64_t)items[i].n_sets * items[i].T * items[i].V3);
-    mbc_status st = ensure(c, c->partials, sizeof(d4) * (size_t)std::max<int64_t>(sites, 1), nullptr);
-    if (st == MBC_OK) st = ensure(c, c->site_tmp, sizeof(d4) * (size_t)std::max<int64_t>(sites, 1), nullptr);
+    for (int i = 0; i < n_items; ++i) {
+        const mbc_work& w = items[i];
+        if (!w.plan || w.plan->ctx != c) return fail(c, MBC_INVALID_ARG, "item plan of another context");
+        if (w.plan->hp.algo != MBC_ALGO_EGRAPH) return fail(c, MBC_UNSUPPORTED, "batched items must use MBC_ALGO_EGRAPH");
+        if (w.n_sets < 0 || w.T < 0 || w.V3 < 0) return fail(c, MBC_INVALID_ARG, "negative item size");
+        const int64_t ns = (int64_t)w.n_sets * w.T * w.V3;
+        if ((ns && (!w.U || !w.D)) || ((int64_t)w.n_sets * w.T && !w.C)) return fail(c, MBC_INVALID_ARG, "null item buffer");
+    }
+    return MBC_OK;
+}
+}  // namespace
+
+mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
+    if (!c) return MBC_INVALID_ARG;
+    mbc_status st = check_items(c, items, n_items);
+    if (st != MBC_OK) return st;
+    cudaSetDevice(c->device);
+    // partial sums of every item, one K slot size for all, item tables per precision
+    int64_t total = 0, kslot = 1;
+    size_t smem[2] = {0, 0};
+    std::vector<int64_t> part_off(n_items);
+    for (int i = 0; i < n_items; ++i) {
+        part_off[i] = total;
+        total += (int64_t)items[i].n_sets * items[i].T * items[i].V3;
+        kslot = std::max<int64_t>(kslot, (int64_t)items[i].plan->ed.n_cols_b * items[i].plan->ed.n_rows_b);
+        const int pr = items[i].plan->hp.prec;
+        smem[pr] = std::max(smem[pr], egraph_smem_bytes(items[i].plan->ed, pr));
+    }
+    const size_t max_smem = std::max(smem[0], smem[1]);
+    const int by_smem = (int)(225 * 1024 / (max_smem + 3 * 1024));
+    const int bps = std::max(1, std::min(by_smem, 2048 / 384));
+    const int grid = std::max(1, c->sms * bps);
+    st = ensure(c, c->batch_parts, sizeof(d4) * (size_t)std::max<int64_t>(total, 1), nullptr);
+    if (st == MBC_OK) st = ensure(c, c->batch_k, (size_t)kslot * 16 * grid, nullptr);
     if (st == MBC_OK) st = ensure(c, c->counter, 256, nullptr);
-    return st;
+    if (st == MBC_OK) st = ensure(c, c->batch_items, sizeof(BatchItem) * (size_t)std::max(n_items, 1) * 2, nullptr);
+    if (st != MBC_OK) return st;
+    for (int pr = 0; pr < 2; ++pr) {
+        c->batch_host[pr].clear();
+        int64_t units = 0;
+        for (int i = 0; i < n_items; ++i) {
+            if (items[i].plan->hp.prec != pr || items[i].plan->hp.terms.empty()) continue;
+            BatchItem b;
+            b.d = items[i].plan->ed;
+            b.U = (const double*)items[i].U;
+            b.D = (const double*)items[i].D;
+            b.part = (d4*)c->batch_parts.p + part_off[i];
+            b.unit_begin = units;
+            units += (int64_t)items[i].n_sets * items[i].T * items[i].V3;
+            c->batch_host[pr].push_back(b);
+        }
+        c->batch_units[pr] = units;
+        c->batch_smem[pr] = smem[pr];
+        if (!c->batch_host[pr].empty()) {
+            cudaError_t e = cudaMemcpy((BatchItem*)c->batch_items.p + (size_t)pr * std::max(n_items, 1),
+                                       c->batch_host[pr].data(), sizeof(BatchItem) * c->batch_host[pr].size(),
+                                       cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(c, e, "item table upload");
+        }
+    }
+    c->batch_kslot = kslot;
+    c->batch_grid = grid;
+    c->batch_reserved.assign(items, items + n_items);
+    c->err.clear();
+    return MBC_OK;
 }
 
 mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream stream) {
     if (!c) return MBC_INVALID_ARG;
-    if (n_items < 0 || (n_items && !items)) return fail(c, MBC_INVALID_ARG, "bad items");
-    for (int i = 0; i < n_items; ++i) {
-        if (!items[i].plan || items[i].plan->ctx != c) return fail(c, MBC_INVALID_ARG, "item plan of another context");
-        if (items[i].plan->hp.algo != MBC_ALGO_EGRAPH) return fail(c, MBC_UNSUPPORTED, "batched items must use MBC_ALGO_EGRAPH");
-    }
-    for (int i = 0; i < n_items; ++i) {
-        const mbc_work& w = items[i];
-        mbc_status st = mbc_correlator(w.plan, w.U, w.D, w.n_sets, w.T, w.V3, w.C, nullptr, stream);
+    mbc_status st = check_items(c, items, n_items);
+    if (st != MBC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!same_items(c->batch_reserved, items, n_items)) {
+        if (capturing(s))
+            return fail(c, MBC_OOM, "mbc_batch inside a stream capture needs mbc_batch_reserve with the same items first");
+        st = mbc_batch_reserve(c, items, n_items);
         if (st != MBC_OK) return st;
     }
+    cudaSetDevice(c->device);
+    const int n_slots = std::max(n_items, 1);
+    // one persistent launch per precision over every (item, site) unit
+    for (int pr = 0; pr < 2; ++pr) {
+        if (c->batch_host[pr].empty()) continue;
+        cudaError_t e = launch_egraph_batch((const BatchItem*)c->batch_items.p + (size_t)pr * n_slots,
+                                            (int)c->batch_host[pr].size(), c->batch_units[pr], pr, 384, c->batch_grid,
+                                            c->batch_smem[pr], (unsigned int*)c->counter.p, c->batch_k.p,
+                                            c->batch_kslot, s, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(c, e, "batched kernel launch");
+    }
+    // site sums per item
+    int64_t off = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const mbc_work& w = items[i];
+        Geometry g{w.n_sets, w.T, w.V3};
+        const HostPlan& h = w.plan->hp;
+        const cd scale = cd_make(h.scale.real(), h.scale.imag());
+        if (h.terms.empty() || g.n_sites() == 0) {
+            if ((int64_t)w.n_sets * w.T) {
+                cudaError_t e = cudaMemsetAsync(w.C, 0, sizeof(double2) * (size_t)w.n_sets * w.T, s);
+                if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+            }
+        } else {
+            Partials pt{(d4*)c->batch_parts.p + off, 1};
+            cudaError_t e = launch_reduce(pt, g, scale, (double2*)w.C, nullptr, nullptr, s, &c->launches);
+            if (e != cudaSuccess) return cuda_fail(c, e, "reduction launch");
+        }
+        off += g.n_sites();
+    }
+    c->err.clear();
     return MBC_OK;
 }
 

@@ -93,6 +93,16 @@ struct EgraphDev {
     int smem_values;                 // total complex values in dynamic shared memory
 };
 
+// One item of a batched launch: a plan's device view, its fields, where its per-site
+// partials go, and the number of the item's first work unit (site).
+struct BatchItem {
+    EgraphDev d;
+    const double* U;
+    const double* D;
+    d4* part;
+    int64_t unit_begin;
+};
+
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_direct(const DirectDev& d, int prec, const double* U, const double* D, Geometry g,
                           int64_t chunk, Partials out, int threads, cudaStream_t s, int64_t* launches);
@@ -104,6 +114,9 @@ cudaError_t launch_egraph(const EgraphDev& d, int prec, const double* U, const d
                           Partials out, int threads, int grid, unsigned int* counter, void* kscratch,
                           cudaStream_t s, int64_t* launches);
 size_t egraph_smem_bytes(const EgraphDev& d, int prec);
+cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_units, int prec, int threads, int grid,
+                                size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values, cudaStream_t s,
+                                int64_t* launches);
 size_t egraph_kslot_bytes(const EgraphDev& d);
 cudaError_t launch_reduce(Partials in, Geometry g, cd scale, double2* C, double2* site_out, d4* site_tmp,
                           cudaStream_t s, int64_t* launches);

@@ -96,139 +96,192 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
     }
 }
 
+// One sink site: stage, phase 1 (A tree, K updates), phase 2 (B tree, dots), site sum.
 template <class P>
-__global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* __restrict__ U,
-                                                     const double* __restrict__ D, Geometry g, Partials out,
-                                                     unsigned int* __restrict__ counter,
-                                                     typename P::V* __restrict__ kscratch) {
+__device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __restrict__ U,
+                                            const double* __restrict__ D, int64_t site, d4* part,
+                                            typename P::V* __restrict__ kslot, unsigned char* smem_raw, double* red) {
     typedef typename P::V V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // shared memory: the two staged blocks, the A stack (levels 0..nA-1 and two buffers
-    // for the leaf level), the B stack (likewise), and G for the general leaf path
     V* sA = reinterpret_cast<V*>(smem_raw);
     V* sB = sA + kBlk;
     V* stA = sB + kBlk;
     V* stB = stA + d.stack_a;
     V* G = stB + d.stack_b;
-    __shared__ double red[4 * 32];
-    __shared__ unsigned int s_unit;
     const int nA = d.A.n, nB = d.B.n;
     const int n_rb = d.n_rows_b, nj = d.n_j;
     const bool fused = d.compact && nj <= 2;
-    V* K = kscratch + (size_t)blockIdx.x * d.n_cols_b * n_rb;      // this block's K slot
+    V* K = kslot;
+    // ---- stage the site's blocks (A flavour first)
+    const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
+    const double* mb = (d.flav_a == 0 ? D : U) + site * 288;
+    int ea, eb;
+    load_pair<P>(ma, mb, sA, sB, red, ea, eb);
+    if (threadIdx.x == 0) {
+        stA[0] = P::one();
+        stB[0] = P::one();
+    }
+    __syncthreads();
+    // ---- phase 1: A column tree, G_j per leaf, K updates per pair
+    int parity = 0;
+    for (int nd = 0; nd < d.A.n_nodes; ++nd) {
+        const int k = __ldg(d.A.node_level + nd);
+        // leaf-level tables alternate between two buffers, so the next leaf's Laplace
+        // step may start while slower threads still read this leaf's table
+        V* dest = stA + d.A.off[k] + (k == nA ? parity * d.A.size[nA] : 0);
+        laplace_level<P>(d.A, k, __ldg(d.A.node_col + nd), __ldg(d.A.node_sign + nd), sA, stA + d.A.off[k - 1],
+                         dest);
+        __syncthreads();
+        const int leaf = __ldg(d.A.node_leaf + nd);
+        if (leaf < 0) continue;
+        const V* T = dest;
+        parity ^= 1;
+        if (fused) {
+            if (nj == 1) leaf_fused<P, 1>(d, leaf, T, K);
+            else leaf_fused<P, 2>(d, leaf, T, K);
+            // no barrier: the next leaf writes the other buffer, and the barrier after
+            // the next Laplace step orders these K writes before later K updates
+            continue;
+        }
+        {   // G_j(R_b) = sum_{R_a} s_j(R_a, R_b) T(R_a); flat index it = b * nj + j
+            const int total = n_rb * nj, stride = blockDim.x;
+            int b = threadIdx.x / nj, j = threadIdx.x - (threadIdx.x / nj) * nj;
+            const int db = stride / nj, dj = stride - db * nj;
+            for (int it = threadIdx.x; it < total; it += stride) {
+                typename P::A gj;
+                P::acc_zero(gj);
+                const int e1 = __ldg(d.g_off + it + 1);
+                if (d.real_w) {
+                    for (int e = __ldg(d.g_off + it); e < e1; ++e) P::fma_real(gj, ldv<V>(d.g_w, e), T[__ldg(d.g_a + e)]);
+                } else {
+                    for (int e = __ldg(d.g_off + it); e < e1; ++e) P::fma(gj, ldv<V>(d.g_w, e), T[__ldg(d.g_a + e)]);
+                }
+                G[j * n_rb + b] = P::get(gj);
+                b += db;
+                j += dj;
+                if (j >= nj) { j -= nj; ++b; }
+            }
+        }
+        __syncthreads();
+        {   // K(C_b, :) += sum_j coef_j G_j for each pair of this leaf; flat index bi * n_rb + b
+            const int p0 = __ldg(d.pair_off + leaf), np = __ldg(d.pair_off + leaf + 1) - p0;
+            int bi = threadIdx.x / n_rb, b = threadIdx.x - (threadIdx.x / n_rb) * n_rb;
+            const int dbi = blockDim.x / n_rb, db = blockDim.x - dbi * n_rb;
+            for (int it = threadIdx.x; it < np * n_rb; it += blockDim.x) {
+                const int pr = p0 + bi;
+                typename P::A h;
+                P::acc_zero(h);
+                if (d.real_w) {
+                    for (int j = 0; j < nj; ++j) P::fma_real(h, ldv<V>(d.pair_coef, (int64_t)pr * nj + j), G[j * n_rb + b]);
+                } else {
+                    for (int j = 0; j < nj; ++j) P::fma(h, ldv<V>(d.pair_coef, (int64_t)pr * nj + j), G[j * n_rb + b]);
+                }
+                V* kp = K + (size_t)__ldg(d.pair_b + pr) * n_rb + b;
+                const V hv = P::get(h);
+                *kp = __ldg(d.pair_first + pr) ? hv : P::vadd(*kp, hv);
+                bi += dbi;
+                b += db;
+                if (b >= n_rb) { b -= n_rb; ++bi; }
+            }
+        }
+        // G is rewritten by the next leaf only after the barrier that follows the next
+        // Laplace step, which also orders these K writes before later K updates
+    }
+    __syncthreads();
+    // ---- phase 2: B column tree, <K(C_b, :), det B[:, C_b]> per leaf
+    typename P::A acc;
+    P::acc_zero(acc);
+    if (nB == 0) {
+        if (threadIdx.x == 0) P::add(acc, K[0]);
+    } else {
+        int pb = 0;
+        for (int nd = 0; nd < d.B.n_nodes; ++nd) {
+            const int k = __ldg(d.B.node_level + nd);
+            V* dest = stB + d.B.off[k] + (k == nB ? pb * d.B.size[nB] : 0);
+            laplace_level<P>(d.B, k, __ldg(d.B.node_col + nd), __ldg(d.B.node_sign + nd), sB, stB + d.B.off[k - 1],
+                             dest);
+            __syncthreads();
+            const int leaf = __ldg(d.B.node_leaf + nd);
+            if (leaf < 0) continue;
+            pb ^= 1;
+            const V* kc = K + (size_t)leaf * n_rb;
+            for (int b = threadIdx.x; b < n_rb; b += blockDim.x) P::fma(acc, kc[b], dest[b]);
+        }
+    }
+    // ---- site value
+    const cd v = P::to_cd(P::get(acc));
+    kacc re, im;
+    block_sum(v, re, im, red);
+    if (threadIdx.x == 0) store_partial(part, re, im, ea * nA + eb * nB);
+    __syncthreads();
+}
+
+template <class P>
+__global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* __restrict__ U,
+                                                     const double* __restrict__ D, Geometry g, Partials out,
+                                                     unsigned int* __restrict__ counter,
+                                                     typename P::V* __restrict__ kscratch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4 * 32];
+    __shared__ unsigned int s_unit;
+    typename P::V* K = kscratch + (size_t)blockIdx.x * d.n_cols_b * d.n_rows_b;      // this block's K slot
     const int64_t n_units = g.n_sites();
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
         __syncthreads();
         const int64_t site = s_unit;
         if (site >= n_units) break;
-        // ---- stage the site's blocks (A flavour first)
-        const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
-        const double* mb = (d.flav_a == 0 ? D : U) + site * 288;
-        int ea, eb;
-        load_pair<P>(ma, mb, sA, sB, red, ea, eb);
-        if (threadIdx.x == 0) {
-            stA[0] = P::one();
-            stB[0] = P::one();
-        }
+        egraph_site<P>(d, U, D, site, out.part + site, K, smem_raw, red);
+    }
+}
+
+// Several (plan, fields) items in one persistent launch: work units are (item, site),
+// numbered item by item; a block takes units from the counter, finds the item by a
+// search over the unit offsets and evaluates the site with that item's plan.
+template <class P>
+__global__ void __launch_bounds__(384) egraph_batch_kernel(const BatchItem* __restrict__ items, int n_items,
+                                                           int64_t n_units, unsigned int* __restrict__ counter,
+                                                           typename P::V* __restrict__ kscratch, int64_t kslot_values) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4 * 32];
+    __shared__ unsigned int s_unit;
+    typename P::V* K = kscratch + (size_t)blockIdx.x * kslot_values;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
         __syncthreads();
-        // ---- phase 1: A column tree, G_j per leaf, K updates per pair
-        int parity = 0;
-        for (int nd = 0; nd < d.A.n_nodes; ++nd) {
-            const int k = __ldg(d.A.node_level + nd);
-            // leaf-level tables alternate between two buffers, so the next leaf's Laplace
-            // step may start while slower threads still read this leaf's table
-            V* dest = stA + d.A.off[k] + (k == nA ? parity * d.A.size[nA] : 0);
-            laplace_level<P>(d.A, k, __ldg(d.A.node_col + nd), __ldg(d.A.node_sign + nd), sA, stA + d.A.off[k - 1],
-                             dest);
-            __syncthreads();
-            const int leaf = __ldg(d.A.node_leaf + nd);
-            if (leaf < 0) continue;
-            const V* T = dest;
-            parity ^= 1;
-            if (fused) {
-                if (nj == 1) leaf_fused<P, 1>(d, leaf, T, K);
-                else leaf_fused<P, 2>(d, leaf, T, K);
-                // no barrier: the next leaf writes the other buffer, and the barrier after
-                // the next Laplace step orders these K writes before later K updates
-                continue;
-            }
-            {   // G_j(R_b) = sum_{R_a} s_j(R_a, R_b) T(R_a); flat index it = b * nj + j
-                const int total = n_rb * nj, stride = blockDim.x;
-                int b = threadIdx.x / nj, j = threadIdx.x - (threadIdx.x / nj) * nj;
-                const int db = stride / nj, dj = stride - db * nj;
-                for (int it = threadIdx.x; it < total; it += stride) {
-                    typename P::A gj;
-                    P::acc_zero(gj);
-                    const int e1 = __ldg(d.g_off + it + 1);
-                    if (d.real_w) {
-                        for (int e = __ldg(d.g_off + it); e < e1; ++e) P::fma_real(gj, ldv<V>(d.g_w, e), T[__ldg(d.g_a + e)]);
-                    } else {
-                        for (int e = __ldg(d.g_off + it); e < e1; ++e) P::fma(gj, ldv<V>(d.g_w, e), T[__ldg(d.g_a + e)]);
-                    }
-                    G[j * n_rb + b] = P::get(gj);
-                    b += db;
-                    j += dj;
-                    if (j >= nj) { j -= nj; ++b; }
-                }
-            }
-            __syncthreads();
-            {   // K(C_b, :) += sum_j coef_j G_j for each pair of this leaf; flat index bi * n_rb + b
-                const int p0 = __ldg(d.pair_off + leaf), np = __ldg(d.pair_off + leaf + 1) - p0;
-                int bi = threadIdx.x / n_rb, b = threadIdx.x - (threadIdx.x / n_rb) * n_rb;
-                const int dbi = blockDim.x / n_rb, db = blockDim.x - dbi * n_rb;
-                for (int it = threadIdx.x; it < np * n_rb; it += blockDim.x) {
-                    const int pr = p0 + bi;
-                    typename P::A h;
-                    P::acc_zero(h);
-                    if (d.real_w) {
-                        for (int j = 0; j < nj; ++j) P::fma_real(h, ldv<V>(d.pair_coef, (int64_t)pr * nj + j), G[j * n_rb + b]);
-                    } else {
-                        for (int j = 0; j < nj; ++j) P::fma(h, ldv<V>(d.pair_coef, (int64_t)pr * nj + j), G[j * n_rb + b]);
-                    }
-                    V* kp = K + (size_t)__ldg(d.pair_b + pr) * n_rb + b;
-                    const V hv = P::get(h);
-                    *kp = __ldg(d.pair_first + pr) ? hv : P::vadd(*kp, hv);
-                    bi += dbi;
-                    b += db;
-                    if (b >= n_rb) { b -= n_rb; ++bi; }
-                }
-            }
-            // G is rewritten by the next leaf only after the barrier that follows the next
-            // Laplace step, which also orders these K writes before later K updates
+        const int64_t unit = s_unit;
+        if (unit >= n_units) break;
+        int lo = 0, hi = n_items - 1;
+        while (lo < hi) {                  // last item whose first unit is <= unit
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].unit_begin <= unit) lo = mid; else hi = mid - 1;
         }
-        __syncthreads();
-        // ---- phase 2: B column tree, <K(C_b, :), det B[:, C_b]> per leaf
-        typename P::A acc;
-        P::acc_zero(acc);
-        if (nB == 0) {
-            if (threadIdx.x == 0) P::add(acc, K[0]);
-        } else {
-            int pb = 0;
-            for (int nd = 0; nd < d.B.n_nodes; ++nd) {
-                const int k = __ldg(d.B.node_level + nd);
-                V* dest = stB + d.B.off[k] + (k == nB ? pb * d.B.size[nB] : 0);
-                laplace_level<P>(d.B, k, __ldg(d.B.node_col + nd), __ldg(d.B.node_sign + nd), sB, stB + d.B.off[k - 1],
-                                 dest);
-                __syncthreads();
-                const int leaf = __ldg(d.B.node_leaf + nd);
-                if (leaf < 0) continue;
-                pb ^= 1;
-                const V* kc = K + (size_t)leaf * n_rb;
-                for (int b = threadIdx.x; b < n_rb; b += blockDim.x) P::fma(acc, kc[b], dest[b]);
-            }
-        }
-        // ---- site value
-        const cd v = P::to_cd(P::get(acc));
-        kacc re, im;
-        block_sum(v, re, im, red);
-        if (threadIdx.x == 0) store_partial(out.part + site, re, im, ea * nA + eb * nB);
-        __syncthreads();
+        const BatchItem& it = items[lo];
+        const int64_t site = unit - it.unit_begin;
+        egraph_site<P>(it.d, it.U, it.D, site, it.part + site, K, smem_raw, red);
     }
 }
 
 size_t egraph_smem_bytes(const EgraphDev& d, int) { return (size_t)d.smem_values * 16; }
 size_t egraph_kslot_bytes(const EgraphDev& d) { return (size_t)d.n_cols_b * d.n_rows_b * 16; }
+
+cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_units, int prec, int threads, int grid,
+                                size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values, cudaStream_t s,
+                                int64_t* launches) {
+    if (n_units == 0) return cudaSuccess;
+    cudaError_t e;
+    if (prec == 0) e = cudaFuncSetAttribute(egraph_batch_kernel<FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else e = cudaFuncSetAttribute(egraph_batch_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    grid = (int)std::min<int64_t>(n_units, grid);
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    if (prec == 0)
+        egraph_batch_kernel<FP64><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cd*)kscratch, kslot_values);
+    else
+        egraph_batch_kernel<MIXED><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cdf*)kscratch, kslot_values);
+    ++*launches;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_egraph(const EgraphDev& d, int prec, const double* U, const double* D, Geometry g, Partials out,
                           int threads, int grid, unsigned int* counter, void* kscratch, cudaStream_t s,

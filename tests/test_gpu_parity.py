@@ -318,3 +318,69 @@ def test_random_complex_factored(ctx, algo, prec):
     ref = scale * onat.direct(3, 2, snk, src, P, U.reshape(-1, 12, 12), D.reshape(-1, 12, 12))
     check(S[0].ravel(), ref, prec)
     plan.destroy()
+
+
+def _batched_items(ctx, prec, n_sets=2):
+    """Items of the batched workload, scaled down: every operator on two lattice sizes,
+    n_sets propagator sets each (seeds and sets as in the workload recipe)."""
+    ops_ = ("proton", "dinucleon_I", "dinucleon_II", "he3_I", "he3_II")
+    items, keep, meta = [], [], []
+    plans = {op: ctx.plan_operator(op, "egraph", prec) for op in ops_}
+    for (L, T) in ((3, 2), (4, 3)):
+        fs = [mi.workload_fields("batched_64", set_index=s, L=L, T=T) for s in range(n_sets)]
+        U = np.stack([f[0] for f in fs])
+        D = np.stack([f[1] for f in fs])
+        Ud, Dd = dev(U), dev(D)
+        keep += [Ud, Dd]
+        for op in ops_:
+            C = torch.zeros(n_sets, T, dtype=torch.complex128, device="cuda")
+            keep.append(C)
+            items.append(dict(plan=plans[op].handle, U=Ud, D=Dd, C=C, n_sets=n_sets, T=T, V3=L ** 3))
+            meta.append((op, U, D))
+    return items, keep, meta, plans
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_workload_one_launch(ctx, prec):
+    from paper_2201_04269_gb300 import abi
+    items, keep, meta, plans = _batched_items(ctx, prec)
+    abi.mbc_batch_reserve(ctx.handle, items)
+    n0 = ctx.launches
+    ctx.batch(items)
+    torch.cuda.synchronize()
+    # one persistent launch for all items (plus one site-sum launch per item)
+    assert ctx.launches - n0 == 1 + sum(1 for op, _, _ in meta if op not in ("dinucleon_II", "he3_II"))
+    for it, (op, U, D) in zip(items, meta):
+        got = it["C"].cpu().numpy()
+        C_sep, S_sep = run(plans[op], U, D)
+        assert np.array_equal(got, C_sep), op          # same arithmetic, same order
+        if op in ("dinucleon_II", "he3_II"):
+            assert np.all(got == 0)
+        else:
+            ref = oracle_sites(op, U[:, :, :3], D[:, :, :3])
+            check(S_sep[:, :, :3].ravel(), ref, prec)
+    for p in plans.values():
+        p.destroy()
+
+
+def test_batched_workload_cuda_graph(ctx):
+    """The batch captured in a CUDA graph and replayed gives the same C."""
+    from paper_2201_04269_gb300 import abi
+    items, keep, meta, plans = _batched_items(ctx, "mixed")
+    abi.mbc_batch_reserve(ctx.handle, items)
+    ctx.batch(items)
+    torch.cuda.synchronize()
+    ref = [it["C"].cpu().numpy().copy() for it in items]
+    for it in items:
+        it["C"].zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        ctx.batch(items, stream=torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    for it, r in zip(items, ref):
+        assert np.array_equal(it["C"].cpu().numpy(), r)
+    for p in plans.values():
+        p.destroy()
