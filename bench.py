@@ -45,9 +45,17 @@ def measured_peaks():
         return {}
 
 
+FP64_FMA_PER_SM = 2              # DFMA per cycle per SM (ncu: sm__sass_thread_inst_executed_op_dfma peak)
+
+
 def fp32_peak_tflops(sm_mhz):
     """FP32 FMA peak from unit counts and clock: SMs x lanes x 2 flop x clock."""
     return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 FMA peak from unit counts and clock: SMs x DFMA/cycle x 2 flop x clock."""
+    return SM_COUNT * FP64_FMA_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 KERNEL_SOURCES = ("egraph.cu", "numeric.cuh", "common.cuh", "device.cuh")
@@ -81,10 +89,11 @@ def recorded_traffic_per_site():
     return vals["bytes"]
 
 
-def fields(set_index, t_list=None):
+def fields(set_index, t_list=None, seed=SEED, kappa=KAPPA, noise=None, lat=None):
     import mbc_inputs as mi
-    U = mi.propagator_field(SEED, set_index, 0, T, L ** 3, KAPPA, None, t_list)
-    D = mi.propagator_field(SEED, set_index, 1, T, L ** 3, KAPPA, None, t_list)
+    Ls, Ts = lat or (L, T)
+    U = mi.propagator_field(seed, set_index, 0, Ts, Ls ** 3, kappa, noise, t_list)
+    D = mi.propagator_field(seed, set_index, 1, Ts, Ls ** 3, kappa, noise, t_list)
     return U, D
 
 
@@ -198,6 +207,17 @@ def main():
     ap.add_argument("--impl", default="mbc", choices=["mbc", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--fp64-slices", type=int, default=4)
+    # other workloads and algorithms (the default is the benchmark's headline configuration)
+    ap.add_argument("--op", default=OPERATOR)
+    ap.add_argument("--algo", default="egraph", choices=["egraph", "tree", "direct"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--lattice", default=f"{L}x{T}", help="L x T, e.g. 16x32")
+    ap.add_argument("--slices", type=int, default=0, help="time slices evaluated (0 = all)")
+    ap.add_argument("--sites", type=int, default=0, help="sink sites per slice (0 = all)")
+    ap.add_argument("--sets", type=int, default=1, help="propagator sets (source times) per GPU")
+    ap.add_argument("--seed", type=int, default=SEED)
+    ap.add_argument("--kappa", type=float, default=KAPPA)
+    ap.add_argument("--noise", type=float, default=None)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -217,15 +237,27 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
 
-    # weak scaling: every rank evaluates its own propagator set (its own source time)
-    U_h, D_h = fields(rank)
-    n_sites = T * L ** 3
-    U = torch.from_numpy(U_h).cuda()[None]
-    D = torch.from_numpy(D_h).cuda()[None]
-    C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    # weak scaling: every rank evaluates its own propagator sets (its own source times)
+    from paper_2201_04269_gb300 import shard
+    Lb, Tb = (int(v) for v in args.lattice.split("x"))
+    t_list = list(range(Tb)) if args.slices <= 0 else [int(t) for t in np.linspace(0, Tb - 1, args.slices).round()]
+    sets = list(shard.local_sets(args.sets * world, rank, world))
+    hs = [fields(si, t_list, args.seed, args.kappa, args.noise, (Lb, Tb)) for si in sets]
+    U_h = np.stack([h[0] for h in hs])
+    D_h = np.stack([h[1] for h in hs])
+    if args.sites > 0:
+        U_h, D_h = np.ascontiguousarray(U_h[:, :, :args.sites]), np.ascontiguousarray(D_h[:, :, :args.sites])
+    del hs
+    n_sets, n_t, n_v = U_h.shape[:3]
+    n_sites = n_sets * n_t * n_v
+    U = torch.from_numpy(U_h).cuda()
+    D = torch.from_numpy(D_h).cuda()
+    C = torch.zeros(n_sets, n_t, dtype=torch.complex128, device="cuda")
     ctx = Context(local)
-    plan = ctx.plan_operator(OPERATOR, "egraph", "mixed")
+    plan = ctx.plan_operator(args.op, args.algo, args.prec)
     info = plan.info
+    headline = (args.op == OPERATOR and args.algo == "egraph" and args.prec == "mixed" and (Lb, Tb) == (L, T)
+                and args.slices <= 0 and args.sites <= 0 and args.sets == 1 and args.noise is None)
 
     def step():
         plan.correlator(U, D, C, stream=stream)
@@ -253,26 +285,30 @@ def main():
         ms = float(t.item())
     clocks = clk.summary()
     C_mixed = C.cpu().numpy()[0].copy()
+    kname = {"egraph": "egraph_kernel", "tree": "minor_table_kernel + tree_walk_kernel",
+             "direct": "direct_kernel"}[args.algo] + ("<MIXED>" if args.prec == "mixed" else "<FP64>")
 
     # dominant kernel alone: the e-graph kernel plus its two small reduction kernels
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     flops = info["flops_per_site"] * n_sites
     achieved = flops / (ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops(sm_max)
-    tps = recorded_traffic_per_site()
+    peak = fp32_peak_tflops(sm_max) if args.prec == "mixed" else fp64_peak_tflops(sm_max)
+    tps = recorded_traffic_per_site() if headline else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None if tps is None else tps * n_sites, "kernel": "egraph_kernel<MIXED>",
+                "traffic": None if tps is None else tps * n_sites, "kernel": kname,
                 "kernel_source_hash": kernel_hash(),
                 "flops_per_site": info["flops_per_site"], "flop_model": "8 flop per complex multiply-add of the plan",
-                "peak_basis": f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz (derived)"}
+                "peak_basis": (f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz (derived)"
+                               if args.prec == "mixed" else
+                               f"FP64: {SM_COUNT} SMs x {FP64_FMA_PER_SM} DFMA/cycle x 2 x {sm_max:.0f} MHz (derived)")}
 
     # FP64 plan on a subset of time slices (same metric), and the mixed error against it
     fp64 = None
-    if args.fp64_slices > 0:
-        ts = list(np.linspace(0, T - 1, args.fp64_slices).round().astype(int))
-        p64 = ctx.plan_operator(OPERATOR, "egraph", "fp64")
-        Us, Ds = U[:, ts].contiguous(), D[:, ts].contiguous()
+    if args.fp64_slices > 0 and args.prec == "mixed" and args.algo == "egraph":
+        ts = list(np.linspace(0, n_t - 1, min(args.fp64_slices, n_t)).round().astype(int))
+        p64 = ctx.plan_operator(args.op, "egraph", "fp64")
+        Us, Ds = U[:1, ts].contiguous(), D[:1, ts].contiguous()
         C64 = torch.zeros(1, len(ts), dtype=torch.complex128, device="cuda")
         p64.correlator(Us, Ds, C64, stream=stream)
         torch.cuda.synchronize()
@@ -283,18 +319,19 @@ def main():
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         c64 = C64.cpu().numpy()[0]
-        err = float(np.max(np.abs(C_mixed[ts] - c64) / np.abs(c64)))
-        n64 = len(ts) * L ** 3
+        err = float(np.max(np.abs(C_mixed[ts] - c64) / np.maximum(np.abs(c64), 1e-300)))
+        n64 = len(ts) * n_v
+        tf64 = p64.info["flops_per_site"] * n64 / (ms64 * 1e-3) / 1e12
         fp64 = {"value": n64 / (ms64 * 1e-3), "unit": UNIT, "time_slices": [int(t) for t in ts],
-                "tflops": p64.info["flops_per_site"] * n64 / (ms64 * 1e-3) / 1e12,
+                "tflops": tf64, "frac_fp64_peak": tf64 / fp64_peak_tflops(sm_max),
                 "mixed_speedup": (n_sites / (ms * 1e-3)) / (n64 / (ms64 * 1e-3)),
                 "rel_err_mixed_vs_fp64": err}
         p64.destroy()
 
     # end to end through the host-buffer entry point (pinned host memory)
-    U_pin = torch.from_numpy(U_h[None]).pin_memory()
-    D_pin = torch.from_numpy(D_h[None]).pin_memory()
-    C_pin = torch.zeros(1, T, dtype=torch.complex128).pin_memory()
+    U_pin = torch.from_numpy(U_h).pin_memory()
+    D_pin = torch.from_numpy(D_h).pin_memory()
+    C_pin = torch.zeros(n_sets, n_t, dtype=torch.complex128).pin_memory()
     plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
     t0 = time.perf_counter()
     e2e_steps = 1
@@ -305,16 +342,23 @@ def main():
            "d2h_bytes_per_step": int(C_pin.numel() * 16)}
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and headline:
         cpu, _ = cpu_baseline()
 
     if rank == 0:
-        line = {"metric": METRIC, "value": world * n_sites / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        metric = METRIC if headline else f"sink-site contractions/sec ({args.op}, {Lb}^3x{Tb}, {args.algo}, {args.prec})"
+        line = {"metric": metric, "value": world * n_sites / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
-                "config": {"workload": f"{OPERATOR} (stand-in for He-3 II) {L}^3x{T}, one source per GPU, "
-                                       f"P+ traced, e-graph plan, mixed (double-float)",
-                           "sites_per_gpu": n_sites, "l2": "inputs 3.2 GB per GPU, larger than L2",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if args.prec == "mixed" else "f64",
+                "data": "synthetic",
+                "config": {"workload": (f"{args.op}" + (" (stand-in for He-3 II)" if args.op == OPERATOR else "") +
+                                        f" {Lb}^3x{Tb}" + (f" ({n_t} slices)" if n_t != Tb else "") +
+                                        (f" ({n_v} sites/slice)" if n_v != Lb ** 3 else "") +
+                                        f", {n_sets} source(s) per GPU, {args.algo} plan, {args.prec}" +
+                                        (f", noise {args.noise}, kappa {args.kappa}" if args.noise else "")),
+                           "sites_per_gpu": n_sites,
+                           "l2": f"inputs {2 * U_h.nbytes / 1e9:.2f} GB per GPU" +
+                                 (", larger than L2" if 2 * U_h.nbytes > 129e6 else ", smaller than L2"),
                            "canonical_terms": info["canonical_terms"], "index_size": info["index_size"]},
                 "roofline": roofline, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks}
