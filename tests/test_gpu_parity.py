@@ -384,3 +384,34 @@ def test_batched_workload_cuda_graph(ctx):
         assert np.array_equal(it["C"].cpu().numpy(), r)
     for p in plans.values():
         p.destroy()
+
+
+@pytest.mark.parametrize("name", ["he3_II_s", "he3_II"])
+def test_config5_noisy_32x64(ctx, name):
+    """3He_II(-s) on 32^3 x 64 with 8 source times, kappa 0.3 and 1e-3 relative noise around a
+    shared base (near-identical sites: every site's rounding adds coherently).  Two time slices
+    of each of the first two sources on the GPU; sampled sites against the oracle, and the
+    mixed C(t) against the FP64 C(t) at the 1e-6 target."""
+    import mbc_inputs as mi_
+    w = mi_.WORKLOADS["he3_32x64_8src"]
+    U = np.stack([mi_.propagator_field(w["seed"], s, 0, 64, 32 ** 3, w["kappa"], w["noise"], [5, 50]) for s in range(2)])
+    D = np.stack([mi_.propagator_field(w["seed"], s, 1, 64, 32 ** 3, w["kappa"], w["noise"], [5, 50]) for s in range(2)])
+    out = {}
+    for prec in ("fp64", "mixed"):
+        plan = ctx.plan_operator(name, "egraph", prec)
+        out[prec] = run(plan, U, D)
+        plan.destroy()
+    if name == "he3_II":
+        assert all(np.all(v[0] == 0) for v in out.values())
+        return
+    C64, S64 = out["fp64"]
+    Cmx, Smx = out["mixed"]
+    assert relerr(Cmx, C64) <= 1e-6
+    assert relerr(Cmx, C64) <= TIGHT_MIXED
+    rng = np.random.default_rng(5)
+    xs = rng.choice(32 ** 3, size=4, replace=False)
+    for s in range(2):
+        for ti in range(2):
+            ref = oracle_sites(name, U[s, ti, xs], D[s, ti, xs])
+            check(S64[s, ti, xs], ref, "fp64")
+            check(Smx[s, ti, xs], ref, "mixed")
