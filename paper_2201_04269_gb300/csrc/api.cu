@@ -265,7 +265,9 @@ mbc_status upload(mbc_plan* P) {
     ed.stack_a = ed.A.off[ed.A.n] + 2 * ed.A.size[ed.A.n];
     ed.stack_b = ed.B.off[ed.B.n] + 2 * ed.B.size[ed.B.n];
     const bool fused = compact && ed.n_j <= 2;
-    ed.smem_values = 2 * kBlk + ed.stack_a + ed.stack_b + (fused ? 0 : ed.n_j * ed.n_rows_b);
+    // plus the packed tables of the two leaf levels (uint32 words, in 16-byte units)
+    const int pk_words = ed.A.size[ed.A.n] * ed.A.n + ed.B.size[ed.B.n] * ed.B.n;
+    ed.smem_values = 2 * kBlk + ed.stack_a + ed.stack_b + (fused ? 0 : ed.n_j * ed.n_rows_b) + (pk_words + 3) / 4;
     return MBC_OK;
 }
 

@@ -28,15 +28,14 @@ namespace mbc {
 
 // One Laplace step for every row set of level K: dest[e] = sum_i (-1)^(i+q) M[r_i, col] parent[c_i].
 template <class P, int K>
-__device__ __forceinline__ void laplace_k(const MinorDev& m, int col, int sign, const typename P::V* mat,
-                                          const typename P::V* parent, typename P::V* dest) {
+__device__ __forceinline__ void laplace_k(const MinorDev& m, const uint32_t* pk, int col, int sign,
+                                          const typename P::V* mat, const typename P::V* parent, typename P::V* dest) {
     const int n = m.size[K];
-    const uint32_t* pk = m.pack[K];
     const typename P::V* mc = mat + col;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         uint32_t w[K];
 #pragma unroll
-        for (int i = 0; i < K; ++i) w[i] = __ldg(pk + e * K + i);
+        for (int i = 0; i < K; ++i) w[i] = pk[e * K + i];
         typename P::A acc;
         P::acc_zero(acc);
 #pragma unroll
@@ -50,16 +49,20 @@ __device__ __forceinline__ void laplace_k(const MinorDev& m, int col, int sign, 
     }
 }
 
+// The leaf level's packed table is read from a shared-memory copy (leaf_pk); the other
+// levels from global memory.
 template <class P>
 __device__ __forceinline__ void laplace_level(const MinorDev& m, int k, int col, int sign, const typename P::V* mat,
-                                              const typename P::V* parent, typename P::V* dest) {
+                                              const typename P::V* parent, typename P::V* dest,
+                                              const uint32_t* leaf_pk) {
+    const uint32_t* pk = k == m.n ? leaf_pk : m.pack[k];
     switch (k) {
-        case 1: laplace_k<P, 1>(m, col, sign, mat, parent, dest); break;
-        case 2: laplace_k<P, 2>(m, col, sign, mat, parent, dest); break;
-        case 3: laplace_k<P, 3>(m, col, sign, mat, parent, dest); break;
-        case 4: laplace_k<P, 4>(m, col, sign, mat, parent, dest); break;
-        case 5: laplace_k<P, 5>(m, col, sign, mat, parent, dest); break;
-        default: laplace_k<P, 6>(m, col, sign, mat, parent, dest); break;
+        case 1: laplace_k<P, 1>(m, pk, col, sign, mat, parent, dest); break;
+        case 2: laplace_k<P, 2>(m, pk, col, sign, mat, parent, dest); break;
+        case 3: laplace_k<P, 3>(m, pk, col, sign, mat, parent, dest); break;
+        case 4: laplace_k<P, 4>(m, pk, col, sign, mat, parent, dest); break;
+        case 5: laplace_k<P, 5>(m, pk, col, sign, mat, parent, dest); break;
+        default: laplace_k<P, 6>(m, pk, col, sign, mat, parent, dest); break;
     }
 }
 
@@ -100,7 +103,8 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
 template <class P>
 __device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __restrict__ U,
                                             const double* __restrict__ D, int64_t site, d4* part,
-                                            typename P::V* __restrict__ kslot, unsigned char* smem_raw, double* red) {
+                                            typename P::V* __restrict__ kslot, unsigned char* smem_raw, double* red,
+                                            const uint32_t** pk_owner) {
     typedef typename P::V V;
     V* sA = reinterpret_cast<V*>(smem_raw);
     V* sB = sA + kBlk;
@@ -111,6 +115,16 @@ __device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __
     const int n_rb = d.n_rows_b, nj = d.n_j;
     const bool fused = d.compact && nj <= 2;
     V* K = kslot;
+    // packed tables of the two leaf levels, copied to shared memory once per plan
+    uint32_t* pkA = reinterpret_cast<uint32_t*>(G + (fused ? 0 : nj * n_rb));
+    uint32_t* pkB = pkA + d.A.size[nA] * nA;
+    if (*pk_owner != d.A.pack[nA]) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < d.A.size[nA] * nA; i += blockDim.x) pkA[i] = __ldg(d.A.pack[nA] + i);
+        for (int i = threadIdx.x; i < d.B.size[nB] * nB; i += blockDim.x) pkB[i] = __ldg(d.B.pack[nB] + i);
+        __syncthreads();
+        if (threadIdx.x == 0) *pk_owner = d.A.pack[nA];
+    }
     // ---- stage the site's blocks (A flavour first)
     const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
     const double* mb = (d.flav_a == 0 ? D : U) + site * 288;
@@ -129,7 +143,7 @@ __device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __
         // step may start while slower threads still read this leaf's table
         V* dest = stA + d.A.off[k] + (k == nA ? parity * d.A.size[nA] : 0);
         laplace_level<P>(d.A, k, __ldg(d.A.node_col + nd), __ldg(d.A.node_sign + nd), sA, stA + d.A.off[k - 1],
-                         dest);
+                         dest, pkA);
         __syncthreads();
         const int leaf = __ldg(d.A.node_leaf + nd);
         if (leaf < 0) continue;
@@ -198,7 +212,7 @@ __device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __
             const int k = __ldg(d.B.node_level + nd);
             V* dest = stB + d.B.off[k] + (k == nB ? pb * d.B.size[nB] : 0);
             laplace_level<P>(d.B, k, __ldg(d.B.node_col + nd), __ldg(d.B.node_sign + nd), sB, stB + d.B.off[k - 1],
-                             dest);
+                             dest, pkB);
             __syncthreads();
             const int leaf = __ldg(d.B.node_leaf + nd);
             if (leaf < 0) continue;
@@ -223,6 +237,8 @@ __global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * 32];
     __shared__ unsigned int s_unit;
+    __shared__ const uint32_t* pk_owner;
+    if (threadIdx.x == 0) pk_owner = nullptr;
     typename P::V* K = kscratch + (size_t)blockIdx.x * d.n_cols_b * d.n_rows_b;      // this block's K slot
     const int64_t n_units = g.n_sites();
     for (;;) {
@@ -230,7 +246,7 @@ __global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* 
         __syncthreads();
         const int64_t site = s_unit;
         if (site >= n_units) break;
-        egraph_site<P>(d, U, D, site, out.part + site, K, smem_raw, red);
+        egraph_site<P>(d, U, D, site, out.part + site, K, smem_raw, red, &pk_owner);
     }
 }
 
@@ -244,6 +260,8 @@ __global__ void __launch_bounds__(384) egraph_batch_kernel(const BatchItem* __re
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * 32];
     __shared__ unsigned int s_unit;
+    __shared__ const uint32_t* pk_owner;
+    if (threadIdx.x == 0) pk_owner = nullptr;
     typename P::V* K = kscratch + (size_t)blockIdx.x * kslot_values;
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
@@ -257,7 +275,7 @@ __global__ void __launch_bounds__(384) egraph_batch_kernel(const BatchItem* __re
         }
         const BatchItem& it = items[lo];
         const int64_t site = unit - it.unit_begin;
-        egraph_site<P>(it.d, it.U, it.D, site, it.part + site, K, smem_raw, red);
+        egraph_site<P>(it.d, it.U, it.D, site, it.part + site, K, smem_raw, red, &pk_owner);
     }
 }
 

@@ -453,21 +453,36 @@ static void build_egraph(HostPlan& p, const std::vector<int>& used_j, const std:
         e.flav_a = fa;
         e.n_j = n_j;
         build_minor_plan(e.A, na, p.rows[fa], p.cols[fa]);
-        build_minor_plan(e.B, nb, p.rows[1 - fa], p.cols[1 - fa]);
-        // K holds |cols_B| x |rows_B| values: prefer the smaller second flavour
+        // B row sets ordered by their number of G entries (most first), so that the
+        // threads of a warp, which own consecutive row sets, do similar work
+        std::vector<Mask> rows_b = p.rows[1 - fa];
+        if (nb) {
+            std::vector<int64_t> cnt(rows_b.size(), 0);
+            for (int j : used_j)
+                for (auto& t : p.snk_can[j]) cnt[fa == 0 ? t.b : t.a] += 1;
+            std::vector<int32_t> order(rows_b.size());
+            for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+            std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cnt[x] > cnt[y]; });
+            for (size_t i = 0; i < order.size(); ++i) rows_b[i] = p.rows[1 - fa][order[i]];
+        }
+        build_minor_plan(e.B, nb, rows_b, p.cols[1 - fa]);
         double cost = egraph_cost(p, fa, e.A, e.B, used_j, used_jp);
         if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = std::move(e); }
     }
     EgraphPlan& e = best;
     const int fa = e.flav_a;
     const int nB = e.B.n;
-    // G entries grouped by (B row set, j): (A row set, w)
+    // G entries grouped by (B row set, j): (A row set, w); B row sets are numbered by
+    // their position in the B plan's leaf level (which the K rows and B tables follow)
     const size_t n_rb = nB ? p.rows[1 - fa].size() : 1;
+    std::vector<int32_t> bpos(n_rb, 0);
+    if (nB)
+        for (size_t i = 0; i < n_rb; ++i) bpos[index_of(p.rows[1 - fa], e.B.level_rows[nB][i])] = (int32_t)i;
     std::vector<std::vector<std::pair<int32_t, cplx>>> byb(n_rb * (size_t)n_j);
     for (int jj = 0; jj < n_j; ++jj)
         for (auto& t : p.snk_can[used_j[jj]]) {
             int32_t a = fa == 0 ? t.a : t.b, b = fa == 0 ? t.b : t.a;
-            byb[(size_t)(nB ? b : 0) * n_j + jj].emplace_back(a, t.w);
+            byb[(size_t)(nB ? bpos[b] : 0) * n_j + jj].emplace_back(a, t.w);
         }
     e.g_off.assign(1, 0);
     for (auto& v : byb) {
