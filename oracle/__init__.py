@@ -21,6 +21,8 @@ determinant.  Modules:
 * ``correlator`` the correlator by definition, by the canonical form, per site
 * ``factor_tree`` abstract and linearised factor trees (Sec. 4, Figs. 4-5)
 * ``egraph``     tensor e-graph with union-find, class map and hash-cons (Sec. 5)
+* ``blocks``     hadron blocks, their momentum projection and the expanded block form of
+                 the correlator (Secs. 2-3)
 * ``native``     the same per-site sums written in plain C for speed (``csrc/oracle.c``)
 
 Pins: every function is checked by ``tests/test_oracle_*.py`` against closed forms,
