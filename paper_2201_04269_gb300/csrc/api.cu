@@ -265,9 +265,16 @@ mbc_status upload(mbc_plan* P) {
     ed.stack_a = ed.A.off[ed.A.n] + 2 * ed.A.size[ed.A.n];
     ed.stack_b = ed.B.off[ed.B.n] + 2 * ed.B.size[ed.B.n];
     const bool fused = compact && ed.n_j <= 2;
-    // plus the packed tables of the two leaf levels (uint32 words, in 16-byte units)
-    const int pk_words = ed.A.size[ed.A.n] * ed.A.n + ed.B.size[ed.B.n] * ed.B.n;
-    ed.smem_values = 2 * kBlk + ed.stack_a + ed.stack_b + (fused ? 0 : ed.n_j * ed.n_rows_b) + (pk_words + 3) / 4;
+    const int base = 2 * kBlk + ed.stack_a + ed.stack_b + (fused ? 0 : ed.n_j * ed.n_rows_b);
+    // the packed tables of the two leaf levels (uint32 words, in 16-byte units) go to shared
+    // memory too when that costs no resident block at 384 threads (the double-float kernel
+    // is issue-bound and needs the warps), and always for FP64 (bound by the FP64 pipe,
+    // it gains more from the shorter table reads than it loses in occupancy)
+    const int pk16 = (ed.A.size[ed.A.n] * ed.A.n + ed.B.size[ed.B.n] * ed.B.n + 3) / 4;
+    auto resident = [](int values) { return std::min(225 * 1024 / (values * 16 + 3 * 1024), 2048 / 384); };
+    ed.stage_pk = (base + pk16) * 16 <= 200 * 1024 &&
+                  (h.prec == MBC_PREC_FP64 || resident(base + pk16) >= resident(base));
+    ed.smem_values = base + (ed.stage_pk ? pk16 : 0);
     return MBC_OK;
 }
 

@@ -91,6 +91,7 @@ struct EgraphDev {
     int stack_a;                     // values in the A stack (levels 0..n_A)
     int stack_b;                     // values in the B stack (levels 0..n_B)
     int smem_values;                 // total complex values in dynamic shared memory
+    int stage_pk;                    // copy the leaf-level packed tables to shared memory
 };
 
 // One item of a batched launch: a plan's device view, its fields, where its per-site

@@ -49,7 +49,7 @@ __device__ __forceinline__ void laplace_k(const MinorDev& m, const uint32_t* pk,
     }
 }
 
-// The leaf level's packed table is read from a shared-memory copy (leaf_pk); the other
+// The leaf level's packed table is read from leaf_pk (a shared-memory copy when the plan stages it); the other
 // levels from global memory.
 template <class P>
 __device__ __forceinline__ void laplace_level(const MinorDev& m, int k, int col, int sign, const typename P::V* mat,
@@ -115,15 +115,22 @@ __device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __
     const int n_rb = d.n_rows_b, nj = d.n_j;
     const bool fused = d.compact && nj <= 2;
     V* K = kslot;
-    // packed tables of the two leaf levels, copied to shared memory once per plan
-    uint32_t* pkA = reinterpret_cast<uint32_t*>(G + (fused ? 0 : nj * n_rb));
-    uint32_t* pkB = pkA + d.A.size[nA] * nA;
-    if (*pk_owner != d.A.pack[nA]) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < d.A.size[nA] * nA; i += blockDim.x) pkA[i] = __ldg(d.A.pack[nA] + i);
-        for (int i = threadIdx.x; i < d.B.size[nB] * nB; i += blockDim.x) pkB[i] = __ldg(d.B.pack[nB] + i);
-        __syncthreads();
-        if (threadIdx.x == 0) *pk_owner = d.A.pack[nA];
+    // packed tables of the two leaf levels: copied to shared memory once per plan when the
+    // plan asks for it (when that costs no resident block), else read through L1
+    const uint32_t* pkA = d.A.pack[nA];
+    const uint32_t* pkB = d.B.pack[nB];
+    if (d.stage_pk) {
+        uint32_t* sa = reinterpret_cast<uint32_t*>(G + (fused ? 0 : nj * n_rb));
+        uint32_t* sb = sa + d.A.size[nA] * nA;
+        if (*pk_owner != d.A.pack[nA]) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < d.A.size[nA] * nA; i += blockDim.x) sa[i] = __ldg(d.A.pack[nA] + i);
+            for (int i = threadIdx.x; i < d.B.size[nB] * nB; i += blockDim.x) sb[i] = __ldg(d.B.pack[nB] + i);
+            __syncthreads();
+            if (threadIdx.x == 0) *pk_owner = d.A.pack[nA];
+        }
+        pkA = sa;
+        pkB = sb;
     }
     // ---- stage the site's blocks (A flavour first)
     const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
