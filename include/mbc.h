@@ -246,6 +246,79 @@ mbc_status mbc_get_schedule(const mbc_plan* plan, mbc_schedule* s);
 mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, const void* D, int n_sets, int T, int64_t V3,
                                   void* C, mbc_stream stream);
 
+/* ------------------------------------------------------------------------------------
+ * Hadron blocks (Sec. 2) and the block form of the correlator (Secs. 3-4).
+ *
+ * The block of a baryon B = eps_abc (q1_a^T G q2_b) q3_c^alpha with q3 = q1, at sink
+ * site x (the proton block equation of Sec. 2):
+ *     f(x; s1, s2, s3)_alpha = < B_alpha(x) qbar1(s1) qbar2(s2) qbar3(s3) >
+ *       = eps_abc G_{beta gamma} [ Q1[(a beta), s3] Q1[(c alpha), s1]
+ *                                  - Q1[(a beta), s1] Q1[(c alpha), s3] ] Q2[(b gamma), s2]
+ * with Q1, Q2 the propagators of flavours q1, q2 at x, row (colour a, spin beta) =
+ * 3 beta + a and source indices s = 3 spin + colour.  Types: P (q1 = u, q2 = d) and N
+ * (q1 = d, q2 = u), each with G = C gamma_5, C gamma_5 P_+ or C gamma_5 P_-.  Entry
+ * eta = ((s1 * 12 + s2) * 12 + s3) * 4 + alpha; MBC_BLOCK_ENTRIES entries per block.
+ * Arithmetic: complex double.
+ *
+ * mbc_hadron_blocks: per-site blocks of one type, f [n_sites][MBC_BLOCK_ENTRIES] complex
+ * double (device, written), from U, D [n_sites][12][12] (device).
+ *
+ * mbc_hadron_blocks_projected: F[s][t] = sum_x e^{-i 2 pi p.x / L} f(x) over the L^3
+ * sink sites of each time slice, site i of the field layout at x = (i mod L,
+ * (i / L) mod L, i / L^2); p: three integers (host memory) or NULL for zero momentum;
+ * U, D [n_sets][T][L^3][12][12]; F [n_sets][T][MBC_BLOCK_ENTRIES] complex double
+ * (device, written).  Partial sums over fixed tiles of sites are combined in a fixed
+ * order with compensated sums (bit-reproducible for given sizes and device).
+ *
+ * Block plans (host planner, once per operator): the expanded block form of an
+ * operator of the library (Sec. 3).  The sink operator is a sum of products of A
+ * baryons whose spins are tied by the operator's tensors; the source operator is the
+ * one of mbc_operator_terms (conjugated sink weights), first put in canonical form
+ * (ascending slot sets, sorting sign; the contraction is antisymmetric in same-flavour
+ * source fields).  Wick's theorem hands the source fields to the sink baryons in N_w
+ * ways per product (9 for dinucleon I, 360 for 3He), each with the sign of the source
+ * reordering times (-1)^{A(A-1)/2}; every term becomes a string of A block entries,
+ * ordered canonically (ascending type, then eta) and merged with its multiplicity; the
+ * merged terms form a factor tree (Sec. 4).
+ *
+ * mbc_block_correlator evaluates, for every set s and time slice t,
+ *     C[s][t] = sum_k w_k prod_i F^{h_ik}[s][t](eta_ik)
+ * with every sink baryon projected to momentum p (p, U, D, C as above; C device complex
+ * double [n_sets][T], written): the paper's block setting.  On an L = 1 lattice it
+ * equals the local-sink correlator of mbc_correlator.  prec must be MBC_PREC_FP64.
+ * ---------------------------------------------------------------------------------- */
+#define MBC_BLOCK_ENTRIES 6912
+typedef enum {
+    MBC_BLOCK_P = 0, MBC_BLOCK_N = 1, MBC_BLOCK_P_PLUS = 2, MBC_BLOCK_P_MINUS = 3,
+    MBC_BLOCK_N_PLUS = 4, MBC_BLOCK_N_MINUS = 5
+} mbc_block_type;
+typedef struct mbc_block_plan mbc_block_plan;
+
+mbc_status mbc_hadron_blocks(mbc_ctx* ctx, int type, const void* U, const void* D, int64_t n_sites, void* f,
+                             mbc_stream stream);
+mbc_status mbc_hadron_blocks_projected(mbc_ctx* ctx, int type, const void* U, const void* D, int n_sets, int T,
+                                       int L, const int* p, void* F, mbc_stream stream);
+
+mbc_status mbc_block_plan_create(mbc_ctx* ctx, int op, int prec, mbc_block_plan** out);
+void mbc_block_plan_destroy(mbc_block_plan* plan);
+typedef struct {
+    int n_baryons;               /* A */
+    int n_products;              /* baryon products of the sink operator */
+    int n_w[8];                  /* source assignments (N_w) of the first 8 products */
+    int64_t expanded_terms;      /* terms before merging */
+    int64_t merged_terms;        /* after merging: the factor tree's leaves */
+    int64_t factors;             /* distinct block entries the terms use */
+    int64_t level_nodes[4];      /* factor-tree vertices per level (level A-1: leaves) */
+    double block_flops_per_site; /* projected blocks of the used entries, per sink site */
+    double tree_flops_per_slice; /* factor-tree evaluation, per time slice */
+} mbc_block_plan_info;
+mbc_status mbc_block_plan_get_info(const mbc_block_plan* plan, mbc_block_plan_info* info);
+/* Merged terms: ids [merged_terms][A] (type * MBC_BLOCK_ENTRIES + eta, ascending within
+ * a term), w [merged_terms][2] complex double (normalisation included); host memory. */
+mbc_status mbc_block_plan_get_terms(const mbc_block_plan* plan, int32_t* ids, double* w);
+mbc_status mbc_block_correlator(mbc_block_plan* plan, const void* U, const void* D, int n_sets, int T, int L,
+                                const int* p, void* C, mbc_stream stream);
+
 /* Number of device kernel launches made by this context since it was created (every
  * launch of every mbc call counts once). */
 int64_t mbc_launch_count(const mbc_ctx* ctx);

@@ -54,6 +54,20 @@ class Context:
     def batch(self, items, stream=None):
         abi.mbc_batch(self.handle, items, stream)
 
+    def block_plan(self, name: str, prec="fp64"):
+        """Block form of a library operator (hadron blocks, Secs. 2-4)."""
+        return BlockPlan(self, abi.mbc_block_plan_create(self.handle, name, prec))
+
+    def hadron_blocks(self, block_type, U, D, f, stream=None):
+        """Per-site blocks: U, D cuda complex128 [..., 12, 12]; f [..., 6912]."""
+        n_sites = U.numel() // 144
+        abi.mbc_hadron_blocks(self.handle, block_type, U, D, n_sites, f, stream)
+
+    def hadron_blocks_projected(self, block_type, U, D, F, L, p=None, stream=None):
+        """Projected blocks: U, D [n_sets, T, L^3, 12, 12]; F [n_sets, T, 6912]."""
+        n_sets, T = U.shape[:2]
+        abi.mbc_hadron_blocks_projected(self.handle, block_type, U, D, n_sets, T, L, F, p, stream)
+
 
 class Plan:
     def __init__(self, ctx: Context, handle):
@@ -88,4 +102,27 @@ class Plan:
         return abi.mbc_plan_get_tree(self.handle)
 
 
-__all__ = ["abi", "Context", "Plan", "MbcError", "ALGO", "PREC", "OPERATOR"]
+class BlockPlan:
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def destroy(self):
+        if self.handle:
+            abi.mbc_block_plan_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def info(self):
+        return abi.mbc_block_plan_get_info(self.handle)
+
+    def terms(self):
+        return abi.mbc_block_plan_get_terms(self.handle)
+
+    def correlator(self, U, D, C, L, p=None, stream=None):
+        """Every sink baryon projected to momentum p: U, D [n_sets, T, L^3, 12, 12]; C [n_sets, T]."""
+        n_sets, T = U.shape[:2]
+        abi.mbc_block_correlator(self.handle, U, D, n_sets, T, L, C, p, stream, self.ctx.handle)
+
+
+__all__ = ["abi", "Context", "Plan", "BlockPlan", "MbcError", "ALGO", "PREC", "OPERATOR"]

@@ -27,6 +27,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "
 ALGO = {"direct": 0, "tree": 1, "egraph": 2}
 PREC = {"fp64": 0, "mixed": 1}
 OPERATOR = {"proton": 0, "neutron": 1, "dinucleon_I": 2, "dinucleon_II": 3, "he3_I": 4, "he3_II": 5, "he3_II_s": 6}
+BLOCK_TYPE = {"P": 0, "N": 1, "P+": 2, "P-": 3, "N+": 4, "N-": 5}
+BLOCK_ENTRIES = 6912
 
 
 class MbcError(RuntimeError):
@@ -64,6 +66,19 @@ class mbc_work(ctypes.Structure):
                 ("V3", ctypes.c_int64), ("C", c_vp)]
 
 
+class mbc_block_plan_info(ctypes.Structure):
+    _fields_ = [("n_baryons", ctypes.c_int), ("n_products", ctypes.c_int), ("n_w", ctypes.c_int * 8),
+                ("expanded_terms", ctypes.c_int64), ("merged_terms", ctypes.c_int64), ("factors", ctypes.c_int64),
+                ("level_nodes", ctypes.c_int64 * 4), ("block_flops_per_site", ctypes.c_double),
+                ("tree_flops_per_slice", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["n_w"] = list(self.n_w)[:self.n_products]
+        d["level_nodes"] = list(self.level_nodes)[:self.n_baryons]
+        return d
+
+
 # (name, restype, argtypes) of every exported entry point
 SIGNATURES = [
     ("mbc_create", ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int]),
@@ -90,6 +105,15 @@ SIGNATURES = [
     ("mbc_get_schedule", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_schedule)]),
     ("mbc_launch_count", ctypes.c_int64, [c_vp]),
     ("mbc_correlator_noalloc", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, c_vp, c_vp]),
+    ("mbc_hadron_blocks", ctypes.c_int, [c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp]),
+    ("mbc_hadron_blocks_projected", ctypes.c_int, [c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, c_i32p, c_vp, c_vp]),
+    ("mbc_block_plan_create", ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(c_vp)]),
+    ("mbc_block_plan_destroy", None, [c_vp]),
+    ("mbc_block_plan_get_info", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_block_plan_info)]),
+    ("mbc_block_plan_get_terms", ctypes.c_int, [c_vp, c_i32p, c_dp]),
+    ("mbc_block_correlator", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_i32p,
+                                            c_vp, c_vp]),
 ]
 
 _LIB = None
@@ -309,3 +333,52 @@ def mbc_get_schedule(plan):
     s = mbc_schedule()
     check(load().mbc_get_schedule(plan, ctypes.byref(s)))
     return dict(threads=s.threads, blocks_per_sm=s.blocks_per_sm, sites_per_unit=s.sites_per_unit)
+
+
+# ------------------------------------------------------------------- hadron blocks
+def _mom(p):
+    if p is None:
+        return None
+    a = (ctypes.c_int32 * 3)(*[int(v) for v in p])
+    return ctypes.cast(a, c_i32p)
+
+
+def mbc_hadron_blocks(ctx, block_type, U, D, n_sites, f, stream=None):
+    check(load().mbc_hadron_blocks(ctx, _enum(BLOCK_TYPE, block_type), dptr(U), dptr(D), n_sites, dptr(f),
+                                   sptr(stream)), ctx)
+
+
+def mbc_hadron_blocks_projected(ctx, block_type, U, D, n_sets, T, L, F, p=None, stream=None):
+    check(load().mbc_hadron_blocks_projected(ctx, _enum(BLOCK_TYPE, block_type), dptr(U), dptr(D), n_sets, T, L,
+                                             _mom(p), dptr(F), sptr(stream)), ctx)
+
+
+def mbc_block_plan_create(ctx, op, prec="fp64"):
+    plan = c_vp()
+    check(load().mbc_block_plan_create(ctx, _enum(OPERATOR, op), _enum(PREC, prec), ctypes.byref(plan)), ctx)
+    return plan.value
+
+
+def mbc_block_plan_destroy(plan):
+    load().mbc_block_plan_destroy(plan)
+
+
+def mbc_block_plan_get_info(plan):
+    info = mbc_block_plan_info()
+    check(load().mbc_block_plan_get_info(plan, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def mbc_block_plan_get_terms(plan):
+    """Merged block terms: (ids int32 [K, A], w complex128 [K])."""
+    info = mbc_block_plan_get_info(plan)
+    K, A = info["merged_terms"], info["n_baryons"]
+    ids = np.zeros((K, A), np.int32)
+    w = np.zeros(K, np.complex128)
+    if K:
+        check(load().mbc_block_plan_get_terms(plan, ids.ctypes.data_as(c_i32p), w.view(np.float64).ctypes.data_as(c_dp)))
+    return ids, w
+
+
+def mbc_block_correlator(plan, U, D, n_sets, T, L, C, p=None, stream=None, ctx=None):
+    check(load().mbc_block_correlator(plan, dptr(U), dptr(D), n_sets, T, L, _mom(p), dptr(C), sptr(stream)), ctx)

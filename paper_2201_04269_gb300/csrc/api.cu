@@ -12,35 +12,9 @@
 #include "device.cuh"
 #include "plan.hpp"
 #include "noalloc.hpp"
+#include "ctx.hpp"
 
 using namespace mbc;
-
-namespace {
-
-// A growable device buffer of the context's pool.
-struct Buf {
-    void* p = nullptr;
-    size_t n = 0;
-};
-
-}  // namespace
-
-struct mbc_ctx {
-    int device = 0;
-    std::string err;
-    int64_t launches = 0;
-    int sms = 0;
-    Buf partials, site_tmp, scratch, exps, counter, hU, hD, hC;
-    std::vector<mbc_plan*> plans;
-    std::map<std::string, mbc_schedule> tune_cache;
-    // batched launches: item tables per precision (device) and the reserved item list
-    Buf batch_items, batch_parts, batch_k;
-    std::vector<mbc_work> batch_reserved;
-    std::vector<BatchItem> batch_host[2];
-    size_t batch_smem[2] = {0, 0};
-    int64_t batch_units[2] = {0, 0}, batch_kslot = 0;
-    int batch_grid = 0;
-};
 
 struct mbc_plan {
     mbc_ctx* ctx = nullptr;
@@ -54,7 +28,7 @@ struct mbc_plan {
     std::string signature;
 };
 
-namespace {
+namespace mbc {
 
 mbc_status fail(mbc_ctx* c, mbc_status s, const std::string& m) {
     if (c) c->err = m;
@@ -89,6 +63,10 @@ mbc_status ensure(mbc_ctx* c, Buf& b, size_t bytes, cudaStream_t s) {
     b.n = want;
     return MBC_OK;
 }
+
+}  // namespace mbc
+
+namespace {
 
 // ---------------------------------------------------------------- device upload
 struct Blob {
@@ -449,14 +427,16 @@ void mbc_destroy(mbc_ctx* c) {
     if (!c) return;
     if (c->device < 0) {
         for (mbc_plan* p : c->plans) delete p;
+        destroy_block_plans(c);
         delete c;
         return;
     }
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (mbc_plan* p : c->plans) { if (p->dev) cudaFree(p->dev); delete p; }
+    destroy_block_plans(c);
     Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
-                   &c->batch_items, &c->batch_parts, &c->batch_k};
+                   &c->batch_items, &c->batch_parts, &c->batch_k, &c->blk_part, &c->blk_F, &c->blk_tree};
     for (Buf* b : bufs) if (b->p) cudaFree(b->p);
     delete c;
 }

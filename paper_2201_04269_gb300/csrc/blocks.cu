@@ -1,0 +1,287 @@
+// blocks.cu - hadron blocks (arXiv 2201.04269 Sec. 2), their momentum projection, and
+// the factor tree over projected blocks (Secs. 3-4).
+//
+// Block of a baryon eps_abc (q1_a^T G q2_b) q3_c^alpha (q3 = q1) at one sink site:
+//     f(s1, s2, s3)_alpha = eps_abc G_{beta gamma} [ Q1[(a beta), s3] Q1[(c alpha), s1]
+//                                      - Q1[(a beta), s1] Q1[(c alpha), s3] ] Q2[(b gamma), s2]
+// Evaluated in two steps per site: the diquark table
+//     Dq[c][s][s2] = sum_{a,b} eps_abc sum_{beta,gamma} G_{beta gamma} Q1[(a beta), s] Q2[(b gamma), s2]
+// (432 entries per block type, two eps terms x nnz(G) products each), then every entry
+//     f(s1, s2, s3)_alpha = sum_c Dq[c][s3][s2] Q1[(c alpha), s1] - Dq[c][s1][s2] Q1[(c alpha), s3]
+// (6 complex multiply-adds).  The site's two propagators and the diquark tables live in
+// shared memory; for the projection each thread owns a fixed set of entries and keeps
+// their running sums over the block's sites in shared memory, so the kernel reads 4.6 KB
+// per site and writes one partial block per tile of sites.  Arithmetic: complex double;
+// the kernel is bound by the FP64 pipe.
+#include "blocks.cuh"
+#include "common.cuh"
+
+namespace mbc {
+
+namespace {
+
+constexpr int kQ = 144;           // one 12 x 12 propagator
+constexpr int kDq = 432;          // one diquark table [c][s][s2]
+constexpr int kThreads = 512;
+constexpr int kTreeThreads = 512;
+constexpr size_t kSmemBudget = 200 * 1024;
+
+__device__ __forceinline__ cd cmul(cd a, cd b) { return cd_make(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+__device__ __forceinline__ void cfma(cd& acc, cd a, cd b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+__device__ __forceinline__ void cfms(cd& acc, cd a, cd b) {
+    acc.re = fma(-a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(-a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// U_x then D_x (complex double, 144 each) into shared memory
+__device__ __forceinline__ void stage_site(const double* __restrict__ U, const double* __restrict__ D, int64_t site,
+                                           cd* q) {
+    const double2* u = reinterpret_cast<const double2*>(U + site * 288);
+    const double2* d = reinterpret_cast<const double2*>(D + site * 288);
+    for (int i = threadIdx.x; i < 2 * kQ; i += blockDim.x) {
+        const double2 v = i < kQ ? __ldg(u + i) : __ldg(d + i - kQ);
+        q[i] = cd_make(v.x, v.y);
+    }
+}
+
+// the block types' tables, copied from the launch parameters to shared memory
+__device__ __forceinline__ void load_types(const BlockDev& b, BlockTypeDev* ty) {
+    if (threadIdx.x < b.n_types) ty[threadIdx.x] = b.t[threadIdx.x];
+}
+
+__device__ __forceinline__ void diquarks(int n_types, const BlockTypeDev* types, const cd* q, cd* dq) {
+    for (int e = threadIdx.x; e < n_types * kDq; e += blockDim.x) {
+        const int t = e / kDq, r = e - t * kDq;
+        const int c = r / 144, s = (r / 12) % 12, s2 = r % 12;
+        const BlockTypeDev& ty = types[t];
+        const cd* q1 = q + ty.q1 * kQ;
+        const cd* q2 = q + (1 - ty.q1) * kQ;
+        const int a0 = (c + 1) % 3, b0 = (c + 2) % 3;   // eps_{a0 b0 c} = +1, eps_{b0 a0 c} = -1
+        cd acc = cd_make(0.0, 0.0);
+        for (int k = 0; k < ty.n; ++k) {
+            const int rb = 3 * ty.be[k], rg = 3 * ty.ga[k];
+            cd x = cmul(q1[(rb + a0) * 12 + s], q2[(rg + b0) * 12 + s2]);
+            const cd y = cmul(q1[(rb + b0) * 12 + s], q2[(rg + a0) * 12 + s2]);
+            x.re -= y.re;
+            x.im -= y.im;
+            cfma(acc, cd_make(ty.g_re[k], ty.g_im[k]), x);
+        }
+        dq[e] = acc;
+    }
+}
+
+__device__ __forceinline__ uint32_t entry_code(const BlockDev& b, int f) {
+    if (b.entry) return __ldg(b.entry + f);
+    const int s1 = f / 576, s2 = (f / 48) % 12, s3 = (f / 4) % 12, al = f % 4;
+    return (uint32_t)((s1 << 12) | (s2 << 8) | (s3 << 4) | al);
+}
+
+__device__ __forceinline__ cd block_entry(const BlockTypeDev* types, uint32_t code, const cd* q, const cd* dq) {
+    const int slot = code >> 16, s1 = (code >> 12) & 15, s2 = (code >> 8) & 15, s3 = (code >> 4) & 15, al = code & 15;
+    const cd* q1 = q + types[slot].q1 * kQ + 3 * al * 12;
+    const cd* d = dq + slot * kDq;
+    cd v = cd_make(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cfma(v, d[c * 144 + s3 * 12 + s2], q1[c * 12 + s1]);
+        cfms(v, d[c * 144 + s1 * 12 + s2], q1[c * 12 + s3]);
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads) block_site_kernel(BlockDev b, const double* __restrict__ U,
+                                                               const double* __restrict__ D, int64_t n_sites,
+                                                               cd* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockTypeDev ty[6];
+    cd* q = reinterpret_cast<cd*>(smem_raw);
+    cd* dq = q + 2 * kQ;
+    load_types(b, ty);
+    for (int64_t site = blockIdx.x; site < n_sites; site += gridDim.x) {
+        __syncthreads();
+        stage_site(U, D, site, q);
+        __syncthreads();
+        diquarks(b.n_types, ty, q, dq);
+        __syncthreads();
+        cd* o = out + site * b.n_f;
+        for (int f = threadIdx.x; f < b.n_f; f += blockDim.x) o[f] = block_entry(ty, entry_code(b, f), q, dq);
+    }
+}
+
+// unit = (slice, tile, entry chunk); part [slice][tile][n_f]
+__global__ void __launch_bounds__(kThreads) block_project_kernel(BlockDev b, const double* __restrict__ U,
+                                                                  const double* __restrict__ D, int64_t V3, int L,
+                                                                  int px, int py, int pz, int tiles, int f_chunk,
+                                                                  int n_fc, cd* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockTypeDev ty[6];
+    cd* q = reinterpret_cast<cd*>(smem_raw);
+    cd* dq = q + 2 * kQ;
+    cd* acc = dq + b.n_types * kDq;
+    load_types(b, ty);
+    const int64_t unit = blockIdx.x;
+    const int fc = (int)(unit % n_fc);
+    const int tile = (int)((unit / n_fc) % tiles);
+    const int64_t slice = unit / ((int64_t)n_fc * tiles);
+    const int f0 = fc * f_chunk;
+    const int nf = min(f_chunk, b.n_f - f0);
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) acc[f] = cd_make(0.0, 0.0);
+    const int64_t x0 = V3 * tile / tiles, x1 = V3 * (tile + 1) / tiles;
+    const bool mom = (px | py | pz) != 0;
+    for (int64_t x = x0; x < x1; ++x) {
+        __syncthreads();
+        stage_site(U, D, slice * V3 + x, q);
+        __syncthreads();
+        diquarks(b.n_types, ty, q, dq);
+        __syncthreads();
+        cd ph = cd_make(1.0, 0.0);
+        if (mom) {
+            const int64_t cx = x % L, cy = (x / L) % L, cz = x / ((int64_t)L * L);
+            int64_t k = ((int64_t)px * cx + (int64_t)py * cy + (int64_t)pz * cz) % L;
+            if (k < 0) k += L;
+            double sn, cs;
+            sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
+            ph = cd_make(cs, sn);
+        }
+        for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+            cd v = block_entry(ty, entry_code(b, f0 + f), q, dq);
+            if (mom) v = cmul(v, ph);
+            acc[f].re += v.re;
+            acc[f].im += v.im;
+        }
+    }
+    cd* o = part + (slice * tiles + tile) * (int64_t)b.n_f + f0;
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) o[f] = acc[f];
+}
+
+// F[slice][f] = sum over tiles in order (compensated)
+__global__ void block_tile_reduce_kernel(const cd* __restrict__ part, int64_t n_slices, int tiles, int n_f,
+                                         cd* __restrict__ F) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slices * n_f) return;
+    const int64_t slice = i / n_f, f = i % n_f;
+    kacc re = {0.0, 0.0}, im = {0.0, 0.0};
+    for (int t = 0; t < tiles; ++t) {
+        const cd v = part[(slice * tiles + t) * n_f + f];
+        kacc_add(re, v.re);
+        kacc_add(im, v.im);
+    }
+    F[i] = cd_make(re.hi + re.lo, im.hi + im.lo);
+}
+
+// unit = (chunk, slice), chunk-major so that the blocks working on one chunk of the tree
+// run together and share its arrays in L2
+template <bool SMEM>
+__global__ void __launch_bounds__(kTreeThreads) block_tree_kernel(BlockTreeDev t, const cd* __restrict__ F,
+                                                                   int64_t n_slices, d4* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4 * (kTreeThreads / 32)];
+    const int64_t chunk = blockIdx.x / n_slices, slice = blockIdx.x % n_slices;
+    const cd* Fs = F + slice * t.n_f;
+    if (SMEM) {
+        cd* fs = reinterpret_cast<cd*>(smem_raw);
+        for (int i = threadIdx.x; i < t.n_f; i += blockDim.x) fs[i] = Fs[i];
+        __syncthreads();
+        Fs = fs;
+    }
+    const int np = t.A - 1;
+    kacc re = {0.0, 0.0}, im = {0.0, 0.0};
+    for (int64_t u = t.chunk_unit[chunk] + threadIdx.x; u < t.chunk_unit[chunk + 1]; u += blockDim.x) {
+        cd pre = cd_make(1.0, 0.0);
+        for (int k = 0; k < np; ++k) pre = cmul(pre, Fs[__ldg(t.unit_pre + u * np + k)]);
+        cd s = cd_make(0.0, 0.0);
+        const int32_t l1 = __ldg(t.unit_leaf + u + 1);
+        for (int32_t l = __ldg(t.unit_leaf + u); l < l1; ++l) {
+            const float2 w = __ldg(t.leaf_w + l);
+            cfma(s, cd_make((double)w.x, (double)w.y), Fs[__ldg(t.leaf_f + l)]);
+        }
+        const cd r = cmul(pre, s);
+        kacc_add(re, r.re);
+        kacc_add(im, r.im);
+    }
+    kacc ore, oim;
+    block_sum(cd_make(re.hi + re.lo, im.hi + im.lo), ore, oim, red);
+    if (threadIdx.x == 0) part[slice * t.n_chunks + chunk] = make_d4(ore.hi, ore.lo, oim.hi, oim.lo);
+}
+
+}  // namespace
+
+int block_entries_per_cta(int n_types) { return (int)(kSmemBudget / 16) - 2 * kQ - n_types * kDq; }
+
+size_t block_kernel_smem(int n_f, int n_types, bool projected) {
+    return (size_t)(2 * kQ + n_types * kDq + (projected ? n_f : 0)) * 16;
+}
+
+namespace {
+void project_shape(int n_f, int n_types, int64_t n_slices, int64_t V3, int sms, int& f_chunk, int& n_fc, int& tiles) {
+    const int cap = block_entries_per_cta(n_types);
+    n_fc = (n_f + cap - 1) / cap;
+    f_chunk = (n_f + n_fc - 1) / n_fc;
+    // about four waves of one resident block per SM, tiles of at least 32 sites
+    const int64_t want = (4LL * sms + n_slices * n_fc - 1) / (n_slices * n_fc);
+    tiles = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max<int64_t>(1, V3 / 32)));
+}
+}  // namespace
+
+int64_t block_project_scratch(int n_f, int n_types, int64_t n_slices, int64_t V3, int sms) {
+    int f_chunk, n_fc, tiles;
+    project_shape(n_f, n_types, n_slices, V3, sms, f_chunk, n_fc, tiles);
+    return n_slices * tiles * (int64_t)n_f;
+}
+
+cudaError_t launch_blocks_site(const BlockDev& b, const double* U, const double* D, int64_t n_sites, cd* out,
+                               int sms, cudaStream_t s, int64_t* launches) {
+    if (n_sites <= 0 || b.n_f <= 0) return cudaSuccess;
+    const size_t smem = block_kernel_smem(b.n_f, b.n_types, false);
+    const int64_t grid = std::min<int64_t>(n_sites, 4LL * sms);
+    block_site_kernel<<<(unsigned)grid, kThreads, smem, s>>>(b, U, D, n_sites, out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blocks_projected(const BlockDev& b, const double* U, const double* D, int64_t n_slices,
+                                    int64_t V3, int L, const int* p, cd* part, cd* F, int sms, cudaStream_t s,
+                                    int64_t* launches) {
+    if (n_slices <= 0 || b.n_f <= 0) return cudaSuccess;
+    if (V3 <= 0) return cudaMemsetAsync(F, 0, sizeof(cd) * (size_t)n_slices * b.n_f, s);
+    int f_chunk, n_fc, tiles;
+    project_shape(b.n_f, b.n_types, n_slices, V3, sms, f_chunk, n_fc, tiles);
+    const size_t smem = block_kernel_smem(f_chunk, b.n_types, true);
+    cudaError_t e = cudaFuncSetAttribute(block_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t units = n_slices * tiles * n_fc;
+    const int px = p ? p[0] : 0, py = p ? p[1] : 0, pz = p ? p[2] : 0;
+    block_project_kernel<<<(unsigned)units, kThreads, smem, s>>>(b, U, D, V3, L, px, py, pz, tiles, f_chunk, n_fc,
+                                                                 part);
+    ++*launches;
+    const int64_t n = n_slices * b.n_f;
+    block_tile_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, n_slices, tiles, b.n_f, F);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_tree(const BlockTreeDev& t, const cd* F, int64_t n_slices, d4* part, cudaStream_t s,
+                              int64_t* launches) {
+    if (n_slices <= 0 || t.n_chunks <= 0) return cudaSuccess;
+    const size_t smem = (size_t)t.n_f * 16;
+    const int64_t grid = (int64_t)t.n_chunks * n_slices;
+    if (smem <= kSmemBudget) {
+        cudaError_t e = cudaFuncSetAttribute(block_tree_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        block_tree_kernel<true><<<(unsigned)grid, kTreeThreads, smem, s>>>(t, F, n_slices, part);
+    } else {
+        block_tree_kernel<false><<<(unsigned)grid, kTreeThreads, 0, s>>>(t, F, n_slices, part);
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace mbc

@@ -1,0 +1,50 @@
+// ctx.hpp - the library context shared by the ABI files (internal).
+#pragma once
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mbc.h"
+#include "device.cuh"
+
+namespace mbc {
+
+// A growable device buffer of the context's pool.
+struct Buf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace mbc
+
+struct mbc_ctx {
+    int device = 0;
+    std::string err;
+    int64_t launches = 0;
+    int sms = 0;
+    mbc::Buf partials, site_tmp, scratch, exps, counter, hU, hD, hC;
+    std::vector<mbc_plan*> plans;
+    std::vector<mbc_block_plan*> block_plans;
+    std::map<std::string, mbc_schedule> tune_cache;
+    // batched launches: item tables per precision (device) and the reserved item list
+    mbc::Buf batch_items, batch_parts, batch_k;
+    std::vector<mbc_work> batch_reserved;
+    std::vector<mbc::BatchItem> batch_host[2];
+    size_t batch_smem[2] = {0, 0};
+    int64_t batch_units[2] = {0, 0}, batch_kslot = 0;
+    int batch_grid = 0;
+    // hadron blocks: per-tile partial blocks, projected blocks, tree partials
+    mbc::Buf blk_part, blk_F, blk_tree;
+};
+
+namespace mbc {
+
+mbc_status fail(mbc_ctx* c, mbc_status s, const std::string& m);
+mbc_status cuda_fail(mbc_ctx* c, cudaError_t e, const char* what);
+bool capturing(cudaStream_t s);
+// Grow a pool buffer to at least `bytes` (never during a stream capture).
+mbc_status ensure(mbc_ctx* c, Buf& b, size_t bytes, cudaStream_t s);
+// Free every block plan of the context (blocks_api.cu).
+void destroy_block_plans(mbc_ctx* c);
+
+}  // namespace mbc

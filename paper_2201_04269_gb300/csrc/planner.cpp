@@ -21,6 +21,7 @@
 //   5. staged contraction for the e-graph kernels: G_j = s_j . A-minors per A column,
 //      then coefficient-weighted dot products with B-minor columns.
 #include "plan.hpp"
+#include "blocks.hpp"
 
 #include <algorithm>
 #include <array>
@@ -252,6 +253,84 @@ std::string operator_terms(int op, int& n_u, int& n_d, int& n_free, std::vector<
     int nq2 = n_u + n_d;
     double wick = ((nq2 * (nq2 - 1) / 2) % 2) ? -1.0 : 1.0;
     scale = wick * norm2;
+    return "";
+}
+
+// ------------------------------------------------------------------------ baryon-level form
+// The same operators as operator_terms, kept as products of baryons (for hadron blocks).
+void block_gamma(int type, GammaNz& out) {
+    static const Dirac dirac;
+    const Mat4& G = (type <= 1) ? dirac.cg5 : (type == 2 || type == 4) ? dirac.cg5p : dirac.cg5m;
+    out.n = 0;
+    for (int be = 0; be < 4; ++be)
+        for (int ga = 0; ga < 4; ++ga)
+            if (G[be][ga] != 0.0) {
+                out.be[out.n] = be;
+                out.ga[out.n] = ga;
+                out.g[out.n] = G[be][ga];
+                ++out.n;
+            }
+}
+
+std::string operator_products(int op, BaryonForm& out) {
+    static const Dirac dirac;
+    enum { P = 0, N = 1, PP = 2, PM = 3, NP = 4 };
+    // X^T (C gamma_5) Y: tie of the first two baryons' spins
+    std::vector<std::pair<std::array<int8_t, 4>, cplx>> tie2;
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+            if (dirac.cg5[a][b] != 0.0) tie2.push_back({{(int8_t)a, (int8_t)b, 0, 0}, dirac.cg5[a][b]});
+    auto single = [&](int type) {
+        BaryonProduct p;
+        p.A = 1;
+        p.types[0] = type;
+        p.tie.resize(4);
+        for (int j = 0; j < 4; ++j) p.tie[j].push_back({{(int8_t)j, 0, 0, 0}, 1.0});
+        return p;
+    };
+    auto two = [&](double coef, int x, int y) {
+        BaryonProduct p;
+        p.coef = coef;
+        p.A = 2;
+        p.types[0] = x; p.types[1] = y;
+        p.tie.assign(1, tie2);
+        return p;
+    };
+    auto three = [&](double coef, int x, int y, int z) {     // X^T Cg5 Y Z^j
+        BaryonProduct p;
+        p.coef = coef;
+        p.A = 3;
+        p.types[0] = x; p.types[1] = y; p.types[2] = z;
+        p.tie.resize(4);
+        for (int j = 0; j < 4; ++j)
+            for (auto& t : tie2) p.tie[j].push_back({{t.first[0], t.first[1], (int8_t)j, 0}, t.second});
+        return p;
+    };
+    out.products.clear();
+    out.norm = 1.0;
+    switch (op) {
+        case 0: out.products.push_back(single(P)); break;
+        case 1: out.products.push_back(single(N)); break;
+        case 2: out.products.push_back(two(1.0, N, P)); break;
+        case 3:
+            out.products.push_back(two(1.0, N, P));
+            out.products.push_back(two(-1.0, P, N));
+            out.norm = 1.0 / std::sqrt(2.0);
+            break;
+        case 4: out.products.push_back(three(1.0, PM, NP, PP)); break;              // + p_-^T Cg5 n_+ p_+^j
+        case 5: case 6:
+            out.products.push_back(three(1.0, PM, NP, PP));                         // + p_-^T Cg5 n_+ p_+^j
+            out.products.push_back(three(-1.0, PP, NP, PM));                        // - p_+^T Cg5 n_+ p_-^j
+            if (op == 5) {
+                out.products.push_back(three(1.0, NP, PP, PM));                     // + n_+^T Cg5 p_+ p_-^j
+                out.products.push_back(three(-1.0, NP, PM, PP));                    // - n_+^T Cg5 p_- p_+^j
+            }
+            out.products.push_back(three(1.0, PP, PM, NP));                         // + p_+^T Cg5 p_- n_+^j
+            if (op == 5) out.products.push_back(three(-1.0, PM, PP, NP));           // - p_-^T Cg5 p_+ n_+^j
+            out.norm = (op == 5) ? 1.0 / std::sqrt(6.0) : 2.0 / std::sqrt(6.0);
+            break;
+        default: return "unknown operator id";
+    }
     return "";
 }
 

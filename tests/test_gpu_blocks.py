@@ -1,0 +1,170 @@
+"""GPU parity of the hadron-block path (arXiv 2201.04269 Secs. 2-4) through the C ABI
+against the oracle (oracle/blocks.py): per-site blocks, momentum-projected blocks, and
+the block form of the correlator; FP64 tolerance 1e-12."""
+import numpy as np
+import pytest
+
+import mbc_inputs as mi
+from oracle import blocks as obl
+from oracle import correlator as ocor
+from oracle import operators as oops
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_04269_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def fields(wl, **kw):
+    U, D = mi.workload_fields(wl, **kw)
+    return U, D
+
+
+def rel(got, want):
+    return float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("h", range(6))
+def test_site_blocks_match_oracle(ctx, h):
+    U, D = fields("dinucleon_16x32", L=2, T=2)          # 16 sites
+    Us, Ds = U.reshape(-1, 12, 12), D.reshape(-1, 12, 12)
+    f = torch.zeros(len(Us), obl.N_ETA, dtype=torch.complex128, device="cuda")
+    ctx.hadron_blocks(h, dev(Us), dev(Ds), f)
+    torch.cuda.synchronize()
+    want = obl.block_site(Us, Ds, h).reshape(len(Us), obl.N_ETA)
+    assert rel(f.cpu().numpy(), want) <= TOL
+
+
+@pytest.mark.parametrize("p", [None, (1, 0, 1), (0, -1, 2)])
+def test_projected_blocks_match_oracle(ctx, p):
+    L = 3
+    U, D = fields("proton_4x8", L=L, T=2)
+    plan = obl.BlockPlan("neutron")
+    want = obl.projected_blocks(plan, U, D, L, p or (0, 0, 0))[:, obl.N_ETA:2 * obl.N_ETA]
+    F = torch.zeros(1, 2, obl.N_ETA, dtype=torch.complex128, device="cuda")
+    ctx.hadron_blocks_projected("N", dev(U[None]), dev(D[None]), F, L, p)
+    torch.cuda.synchronize()
+    assert rel(F.cpu().numpy()[0], want) <= TOL
+
+
+@pytest.mark.parametrize("name,wl,L,T,p", [("proton", "proton_4x8", 4, 3, (1, 2, 0)),
+                                           ("dinucleon_I", "dinucleon_16x32", 4, 2, None),
+                                           ("dinucleon_I", "dinucleon_16x32", 3, 2, (0, 1, 1)),
+                                           ("he3_I", "he3_24x48", 2, 2, None)])
+def test_block_correlator_matches_oracle(ctx, name, wl, L, T, p):
+    U, D = fields(wl, L=L, T=T)
+    ref = obl.BlockPlan(name, "canonical")
+    want = obl.correlator_projected(ref, U, D, L, p or (0, 0, 0))
+    plan = ctx.block_plan(name)
+    C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    plan.correlator(dev(U[None]), dev(D[None]), C, L, p)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()[0]
+    assert np.max(np.abs(got - want) / np.abs(want)) <= TOL
+    plan.destroy()
+
+
+def test_he3_II_s_block_correlator_ragged_lattice(ctx):
+    """3He_II-s on 5^3 x 2: several tiles per slice with a ragged last tile."""
+    L, T = 5, 2
+    U, D = fields("he3_24x48", L=L, t_list=[0, 7])
+    ref = obl.BlockPlan("he3_II_s", "canonical")
+    want = obl.correlator_projected(ref, U, D, L)
+    plan = ctx.block_plan("he3_II_s")
+    C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    plan.correlator(dev(U[None]), dev(D[None]), C, L)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()[0]
+    assert np.max(np.abs(got - want) / np.abs(want)) <= TOL
+    plan.destroy()
+
+
+@pytest.mark.parametrize("name", ["proton", "dinucleon_I", "he3_I"])
+def test_single_site_lattice_equals_local_correlator(ctx, name):
+    """With L = 1 the projected block form is the local-sink correlator of the
+    determinant path (two independent GPU paths and the oracle agree)."""
+    U, D = fields("he3_24x48", L=1, T=4)
+    want = ocor.correlator(ocor.CanonicalPlan(oops.build(name)).site_values, U, D)
+    bp = ctx.block_plan(name)
+    Cb = torch.zeros(1, 4, dtype=torch.complex128, device="cuda")
+    bp.correlator(dev(U[None]), dev(D[None]), Cb, 1)
+    qp = ctx.plan_operator(name, "egraph", "fp64")
+    Cq = torch.zeros(1, 4, dtype=torch.complex128, device="cuda")
+    qp.correlator(dev(U[None]), dev(D[None]), Cq)
+    torch.cuda.synchronize()
+    for got in (Cb.cpu().numpy()[0], Cq.cpu().numpy()[0]):
+        assert np.max(np.abs(got - want) / np.abs(want)) <= TOL
+    bp.destroy()
+    qp.destroy()
+
+
+def test_empty_and_vanishing(ctx):
+    plan = ctx.block_plan("dinucleon_II")                # no block terms at all
+    assert plan.info["merged_terms"] == 0
+    U, D = fields("dinucleon_16x32", L=2, T=2)
+    C = torch.full((1, 2), complex(3.0, 1.0), dtype=torch.complex128, device="cuda")
+    plan.correlator(dev(U[None]), dev(D[None]), C, 2)
+    torch.cuda.synchronize()
+    assert np.all(C.cpu().numpy() == 0)
+    plan.destroy()
+    plan = ctx.block_plan("proton")
+    C = torch.zeros(0, 2, dtype=torch.complex128, device="cuda")
+    plan.correlator(dev(U[None][:0]), dev(D[None][:0]), C, 2)
+    plan.destroy()
+
+
+def test_colour_invariance_full_size(ctx):
+    """At the benchmark size (3He_II-s, 24^3, two slices), S_x -> g_x S_x h^dagger with
+    random SU(3) g_x per site and h at the source leaves C unchanged: a property of the
+    exact correlator at any size."""
+    L = 24
+    t_list = [0, 24]
+    U, D = fields("he3_24x48", t_list=t_list)
+    rng = np.random.default_rng(91)
+    g = mi.su3_random(rng, U.shape[0] * U.shape[1]).reshape(U.shape[0], U.shape[1], 3, 3)
+    h = mi.su3_random(rng, 1)[0]
+    # index i = 3 spin + colour: colour acts as kron(1_spin, g)
+    G = np.einsum("ab,tsxy->tsaxby", np.eye(4), g).reshape(U.shape[0], U.shape[1], 12, 12)
+    H = np.kron(np.eye(4), h)
+
+    def rotate(S):
+        return np.einsum("tsij,tsjk,lk->tsil", G, S, H.conj())
+
+    plan = ctx.block_plan("he3_II_s")
+    C0 = torch.zeros(1, 2, dtype=torch.complex128, device="cuda")
+    C1 = torch.zeros(1, 2, dtype=torch.complex128, device="cuda")
+    plan.correlator(dev(U[None]), dev(D[None]), C0, L)
+    plan.correlator(dev(rotate(U)[None]), dev(rotate(D)[None]), C1, L)
+    torch.cuda.synchronize()
+    a, b = C0.cpu().numpy()[0], C1.cpu().numpy()[0]
+    assert np.all(np.abs(a) > 0)
+    assert np.max(np.abs(a - b) / np.abs(a)) <= 1e-10
+    plan.destroy()
+
+
+def test_block_correlator_deterministic(ctx):
+    U, D = fields("dinucleon_16x32", L=6, T=2)
+    plan = ctx.block_plan("dinucleon_I")
+    outs = []
+    for _ in range(2):
+        C = torch.zeros(1, 2, dtype=torch.complex128, device="cuda")
+        plan.correlator(dev(U[None]), dev(D[None]), C, 6)
+        torch.cuda.synchronize()
+        outs.append(C.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    plan.destroy()
