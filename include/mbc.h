@@ -179,6 +179,14 @@ mbc_status mbc_plan_load(mbc_ctx* ctx, const char* path, mbc_plan** out);
 mbc_status mbc_correlator(mbc_plan* plan, const void* U, const void* D, int n_sets, int T, int64_t V3,
                           void* C, void* site_out, mbc_stream stream);
 
+/* Nonzero sink momentum (the e^{-i p.x} projection of Sec. 2): as mbc_correlator on an
+ * L^3 lattice (V3 = L^3), with C[s][t] = scale * sum_x e^{-i 2 pi p.x / L} C_x(s, t) and
+ * site x of a slice at (x mod L, (x / L) mod L, x / L^2); p: three integers (host
+ * memory), NULL for zero momentum; site_out (optional) receives the site values without
+ * the phase. */
+mbc_status mbc_correlator_momentum(mbc_plan* plan, const void* U, const void* D, int n_sets, int T, int L,
+                                   const int* p, void* C, void* site_out, mbc_stream stream);
+
 /* End to end from host memory: copies U, D (host, pinned or pageable, same layout) to
  * the context's device buffers, evaluates, copies C back to host memory C_host, on
  * the given stream, and synchronises that stream before returning. */

@@ -119,3 +119,17 @@ def correlator(site_fn, U, D):
     T, V3 = U.shape[:2]
     vals = site_fn(U.reshape(-1, 12, 12), D.reshape(-1, 12, 12)).reshape(T, V3)
     return np.array([complex(math.fsum(v.real), math.fsum(v.imag)) for v in vals])
+
+
+def correlator_momentum(site_fn, U, D, L, p):
+    """C(t, p) = sum_x e^{-i 2 pi p.x / L} C_x(t): the sink projected to momentum p (the
+    phase of the momentum projection in Sec. 2); site x of a slice sits at
+    (x mod L, (x / L) mod L, x / L^2).  p = (0, 0, 0) is ``correlator``."""
+    T, V3 = U.shape[:2]
+    assert V3 == L ** 3
+    vals = site_fn(U.reshape(-1, 12, 12), D.reshape(-1, 12, 12)).reshape(T, V3)
+    x = np.arange(V3)
+    k = (p[0] * (x % L) + p[1] * ((x // L) % L) + p[2] * (x // (L * L))) % L
+    phase = np.exp(-2j * np.pi * k / L)
+    return np.array([np.sum(v * phase) for v in vals])
+

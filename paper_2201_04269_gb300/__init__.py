@@ -88,6 +88,11 @@ class Plan:
         n_sets, T, V3 = U.shape[:3]
         abi.mbc_correlator(self.handle, U, D, n_sets, T, V3, C, site_out, stream, self.ctx.handle)
 
+    def correlator_momentum(self, U, D, C, L, p, site_out=None, stream=None):
+        """Sink momentum p (units of 2 pi / L): U, D [n_sets, T, L^3, 12, 12]; C [n_sets, T]."""
+        n_sets, T = U.shape[:2]
+        abi.mbc_correlator_momentum(self.handle, U, D, n_sets, T, L, p, C, site_out, stream, self.ctx.handle)
+
     def correlator_host(self, U, D, C, stream=None):
         n_sets, T, V3 = U.shape[:3]
         abi.mbc_correlator_host(self.handle, U, D, n_sets, T, V3, C, stream, self.ctx.handle)

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("mbc_plan_save", ctypes.c_int, [c_vp, ctypes.c_char_p]),
     ("mbc_plan_load", ctypes.c_int, [c_vp, ctypes.c_char_p, ctypes.POINTER(c_vp)]),
     ("mbc_correlator", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, c_vp, c_vp, c_vp]),
+    ("mbc_correlator_momentum", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_i32p,
+                                               c_vp, c_vp, c_vp]),
     ("mbc_correlator_host", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, c_vp, c_vp]),
     ("mbc_batch_reserve", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_work), ctypes.c_int]),
     ("mbc_batch", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_work), ctypes.c_int, c_vp]),
@@ -290,6 +292,12 @@ def mbc_plan_load(ctx, path):
 
 def mbc_correlator(plan, U, D, n_sets, T, V3, C, site_out=None, stream=None, ctx=None):
     check(load().mbc_correlator(plan, dptr(U), dptr(D), n_sets, T, V3, dptr(C), dptr(site_out), sptr(stream)), ctx)
+
+
+def mbc_correlator_momentum(plan, U, D, n_sets, T, L, p, C, site_out=None, stream=None, ctx=None):
+    """mbc_correlator with the sink momentum phase e^{-i 2 pi p.x / L} in the site sum."""
+    check(load().mbc_correlator_momentum(plan, dptr(U), dptr(D), n_sets, T, L, _mom(p), dptr(C), dptr(site_out),
+                                         sptr(stream)), ctx)
 
 
 def mbc_correlator_noalloc(plan, U, D, n_sets, T, V3, C, stream=None, ctx=None):

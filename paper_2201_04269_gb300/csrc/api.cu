@@ -311,7 +311,7 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
 int64_t direct_chunk(const mbc_plan* P) { return std::max<int64_t>(1, (int64_t)P->sched.sites_per_unit * 65536); }
 
 mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int64_t V3, void* C, void* site_out,
-               cudaStream_t s) {
+               cudaStream_t s, Momentum mom = Momentum()) {
     mbc_ctx* c = P->ctx;
     if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
     HostPlan& h = P->hp;
@@ -366,7 +366,7 @@ mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int
                           c->scratch.p, s, &c->launches);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
-    e = launch_reduce(parts, g, scale, (double2*)C, (double2*)site_out, (d4*)c->site_tmp.p, s, &c->launches);
+    e = launch_reduce(parts, g, scale, (double2*)C, (double2*)site_out, (d4*)c->site_tmp.p, s, &c->launches, mom);
     if (e != cudaSuccess) return cuda_fail(c, e, "reduction launch");
     return MBC_OK;
 }
@@ -620,6 +620,24 @@ mbc_status mbc_correlator(mbc_plan* P, const void* U, const void* D, int n_sets,
     if ((!U || !D) && (int64_t)n_sets * T * V3 > 0) return fail(c, MBC_INVALID_ARG, "null propagator field");
     if ((int64_t)n_sets * T * V3 > ((int64_t)1 << 32)) return fail(c, MBC_UNSUPPORTED, "more than 2^32 sites in one call");
     mbc_status st = run(P, U, D, n_sets, T, V3, C, site_out, (cudaStream_t)stream);
+    if (st == MBC_OK) c->err.clear();
+    return st;
+}
+
+mbc_status mbc_correlator_momentum(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int L, const int* p,
+                                   void* C, void* site_out, mbc_stream stream) {
+    if (!P) return MBC_INVALID_ARG;
+    mbc_ctx* c = P->ctx;
+    if (n_sets < 0 || T < 0 || L < 0) return fail(c, MBC_INVALID_ARG, "negative size");
+    if (L > 1290) return fail(c, MBC_UNSUPPORTED, "L^3 sites per slice beyond the supported range");
+    const int64_t V3 = (int64_t)L * L * L;
+    if (!C && (int64_t)n_sets * T > 0) return fail(c, MBC_INVALID_ARG, "null output");
+    if ((!U || !D) && (int64_t)n_sets * T * V3 > 0) return fail(c, MBC_INVALID_ARG, "null propagator field");
+    if ((int64_t)n_sets * T * V3 > ((int64_t)1 << 32)) return fail(c, MBC_UNSUPPORTED, "more than 2^32 sites in one call");
+    Momentum mom;
+    mom.L = std::max(L, 1);
+    if (p) { mom.px = p[0]; mom.py = p[1]; mom.pz = p[2]; }
+    mbc_status st = run(P, U, D, n_sets, T, V3, C, site_out, (cudaStream_t)stream, mom);
     if (st == MBC_OK) c->err.clear();
     return st;
 }

@@ -83,11 +83,12 @@ __device__ __forceinline__ uint32_t entry_code(const BlockDev& b, int f) {
     return (uint32_t)((s1 << 12) | (s2 << 8) | (s3 << 4) | al);
 }
 
-__device__ __forceinline__ cd block_entry(const BlockTypeDev* types, uint32_t code, const cd* q, const cd* dq) {
+// v + f(entry): the entry's block value added to v (v = 0 for the value itself)
+__device__ __forceinline__ cd block_entry(const BlockTypeDev* types, uint32_t code, const cd* q, const cd* dq,
+                                          cd v = cd_make(0.0, 0.0)) {
     const int slot = code >> 16, s1 = (code >> 12) & 15, s2 = (code >> 8) & 15, s3 = (code >> 4) & 15, al = code & 15;
     const cd* q1 = q + types[slot].q1 * kQ + 3 * al * 12;
     const cd* d = dq + slot * kDq;
-    cd v = cd_make(0.0, 0.0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         cfma(v, d[c * 144 + s3 * 12 + s2], q1[c * 12 + s1]);
@@ -150,11 +151,15 @@ __global__ void __launch_bounds__(kThreads) block_project_kernel(BlockDev b, con
             sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
             ph = cd_make(cs, sn);
         }
-        for (int f = threadIdx.x; f < nf; f += blockDim.x) {
-            cd v = block_entry(ty, entry_code(b, f0 + f), q, dq);
-            if (mom) v = cmul(v, ph);
-            acc[f].re += v.re;
-            acc[f].im += v.im;
+        if (mom) {
+            for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+                const cd v = cmul(block_entry(ty, entry_code(b, f0 + f), q, dq), ph);
+                acc[f].re += v.re;
+                acc[f].im += v.im;
+            }
+        } else {
+            // the running sum is the first addend of the entry's multiply-add chain
+            for (int f = threadIdx.x; f < nf; f += blockDim.x) acc[f] = block_entry(ty, entry_code(b, f0 + f), q, dq, acc[f]);
         }
     }
     cd* o = part + (slice * tiles + tile) * (int64_t)b.n_f + f0;
@@ -221,12 +226,21 @@ size_t block_kernel_smem(int n_f, int n_types, bool projected) {
 
 namespace {
 void project_shape(int n_f, int n_types, int64_t n_slices, int64_t V3, int sms, int& f_chunk, int& n_fc, int& tiles) {
-    const int cap = block_entries_per_cta(n_types);
-    n_fc = (n_f + cap - 1) / cap;
+    const int per_cta = block_entries_per_cta(n_types);
+    n_fc = (n_f + per_cta - 1) / per_cta;
     f_chunk = (n_f + n_fc - 1) / n_fc;
-    // about four waves of one resident block per SM, tiles of at least 32 sites
-    const int64_t want = (4LL * sms + n_slices * n_fc - 1) / (n_slices * n_fc);
-    tiles = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max<int64_t>(1, V3 / 32)));
+    // at least four waves of one resident block per SM, tiles of at least 32 sites, and
+    // among up to four times that many tiles the count whose last wave is fullest
+    const int64_t base = n_slices * n_fc;
+    const int64_t lo = (4LL * std::max(sms, 1) + base - 1) / base, cap = std::max<int64_t>(1, V3 / 32);
+    tiles = (int)std::max<int64_t>(1, std::min(lo, cap));
+    double best = 0.0;
+    for (int64_t t = std::min(lo, cap); t <= std::min(4 * lo, cap); ++t) {
+        const int64_t u = base * t;
+        const double eff = (double)u / (double)(((u + sms - 1) / sms) * sms);
+        if (eff > best + 1e-9) { best = eff; tiles = (int)t; }
+        if (eff >= 0.999) break;
+    }
 }
 }  // namespace
 

@@ -119,7 +119,15 @@ cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_u
                                 size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values, cudaStream_t s,
                                 int64_t* launches);
 size_t egraph_kslot_bytes(const EgraphDev& d);
+// Sink momentum of the site sum: p in units of 2 pi / L, site x of a slice at
+// (x mod L, (x / L) mod L, x / L^2); p = 0 is the plain sum.
+struct Momentum {
+    int L = 1, px = 0, py = 0, pz = 0;
+    __host__ __device__ bool nonzero() const { return (px | py | pz) != 0; }
+};
+// C[set][t] = scale * sum_x e^{-i 2 pi p.x / L} (sum over chunks of the site's partials);
+// site_out (optional) receives scale * the site values without the phase.
 cudaError_t launch_reduce(Partials in, Geometry g, cd scale, double2* C, double2* site_out, d4* site_tmp,
-                          cudaStream_t s, int64_t* launches);
+                          cudaStream_t s, int64_t* launches, Momentum mom = Momentum());
 
 }  // namespace mbc

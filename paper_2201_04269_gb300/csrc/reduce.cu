@@ -1,5 +1,6 @@
 // reduce.cu - site sum of the correlator (arXiv 2201.04269 Eq. 1 summed over the sink
-// sites of a time slice; Sec. 2 with zero momentum).
+// sites of a time slice), with the sink momentum phase e^{-i p.x} of the projection in
+// Sec. 2 (zero momentum: the plain sum).
 //
 // Partials (one per (site, chunk), each a compensated complex double) are combined in a
 // fixed order with TwoSum accumulation: first over the chunks of a site (one thread per
@@ -12,7 +13,8 @@ namespace mbc {
 
 __device__ __forceinline__ cd cmul(cd a, cd b) { return cd_make(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
 
-__global__ void site_reduce_kernel(Partials in, int64_t n_sites, cd scale, d4* site_tmp, double2* site_out) {
+__global__ void site_reduce_kernel(Partials in, int64_t n_sites, int64_t V3, Momentum mom, cd scale, d4* site_tmp,
+                                   double2* site_out) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_sites) return;
     kacc re = {0.0, 0.0}, im = {0.0, 0.0};
@@ -21,10 +23,21 @@ __global__ void site_reduce_kernel(Partials in, int64_t n_sites, cd scale, d4* s
         kacc_merge(re, kacc{v.x, v.y});
         kacc_merge(im, kacc{v.z, v.w});
     }
-    site_tmp[s] = make_d4(re.hi, re.lo, im.hi, im.lo);
     if (site_out) {
         const cd v = cmul(scale, cd_make(re.hi + re.lo, im.hi + im.lo));
         site_out[s] = make_double2(v.re, v.im);
+    }
+    if (mom.nonzero()) {
+        // e^{-i 2 pi p.x / L} with p.x reduced modulo L first (exact argument)
+        const int64_t x = s % V3, L = mom.L;
+        int64_t k = ((int64_t)mom.px * (x % L) + (int64_t)mom.py * ((x / L) % L) + (int64_t)mom.pz * (x / (L * L))) % L;
+        if (k < 0) k += L;
+        double sn, cs;
+        sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
+        const cd v = cmul(cd_make(re.hi + re.lo, im.hi + im.lo), cd_make(cs, sn));
+        site_tmp[s] = make_d4(v.re, 0.0, v.im, 0.0);
+    } else {
+        site_tmp[s] = make_d4(re.hi, re.lo, im.hi, im.lo);
     }
 }
 
@@ -59,13 +72,13 @@ __global__ void slice_reduce_kernel(const d4* __restrict__ sites, int64_t V3, cd
 }
 
 cudaError_t launch_reduce(Partials in, Geometry g, cd scale, double2* C, double2* site_out, d4* site_tmp,
-                          cudaStream_t s, int64_t* launches) {
+                          cudaStream_t s, int64_t* launches, Momentum mom) {
     const int64_t n_sites = g.n_sites();
     const d4* sites = in.part;
-    if (in.n_chunks > 1 || site_out) {
+    if (in.n_chunks > 1 || site_out || mom.nonzero()) {
         const int64_t blocks = (n_sites + 255) / 256;
         if (blocks > 0) {
-            site_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, n_sites, scale, site_tmp, site_out);
+            site_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, n_sites, g.V3, mom, scale, site_tmp, site_out);
             ++*launches;
         }
         sites = site_tmp;

@@ -166,3 +166,27 @@ def test_synthetic_inputs_regenerate_per_site():
     assert np.allclose(mi.site_matrices(2, 0, 0, 4, [3], kappa=0.5) * np.exp(2.0), mi.site_matrices(2, 0, 0, 4, [3], kappa=0.0))
     b = mi.site_matrices(2, 0, 0, 3, [0, 1], kappa=0.3, noise=1e-3)
     assert np.abs(b[0] - b[1]).max() < 1e-2 * np.abs(b[0]).max()
+
+
+def test_momentum_projection_pins(oracle_lib):
+    """Sink momentum (Sec. 2 projection phase): p = 0 is the plain site sum; the sum over
+    all L^3 momenta is L^3 times the value at site 0 (discrete Fourier inversion);
+    translating the fields by a multiplies C(p) by e^{-i 2 pi p.a / L}."""
+    L = 2
+    U, D = mi.workload_fields("proton_4x8", L=L, T=2)
+    plan = cor.CanonicalPlan(ops.build("proton"))
+    c0 = cor.correlator(plan.site_values, U, D)
+    assert close(cor.correlator_momentum(plan.site_values, U, D, L, (0, 0, 0)), c0)
+    total = sum(cor.correlator_momentum(plan.site_values, U, D, L, (a, b, c))
+                for a in range(L) for b in range(L) for c in range(L))
+    site0 = plan.site_values(U[:, 0], D[:, 0])
+    assert close(total, L ** 3 * site0)
+    p, a = (1, 0, 1), np.array([1, 1, 0])
+    x = np.arange(L ** 3)
+    xyz = np.stack([x % L, (x // L) % L, x // (L * L)], axis=1)
+    moved = ((xyz + a) % L) @ np.array([1, L, L * L])
+    Us, Ds = U.copy(), D.copy()
+    Us[:, moved], Ds[:, moved] = U, D
+    cp = cor.correlator_momentum(plan.site_values, U, D, L, p)
+    cs = cor.correlator_momentum(plan.site_values, Us, Ds, L, p)
+    assert close(cs, cp * np.exp(-2j * np.pi * np.dot(p, a) / L))
