@@ -60,22 +60,24 @@ def fp64_peak_tflops(sm_mhz):
 
 KERNEL_SOURCES = ("egraph.cu", "numeric.cuh", "common.cuh", "device.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "egraph_kernel_he3_II_s_24x48.md")
+BLOCK_SOURCES = ("blocks.cu", "blocks.cuh", "numeric.cuh", "common.cuh", "device.cuh")
+BLOCK_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "block_kernels_he3_II_s_24x48.md")
 
 
-def kernel_hash():
+def kernel_hash(sources=KERNEL_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2201_04269_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic_per_site():
+def recorded_traffic_per_site(path=TRAFFIC_FILE, sources=KERNEL_SOURCES):
     """DRAM bytes per site from the committed ncu summary, if the kernel sources are
     unchanged since it was taken (else None)."""
     try:
-        text = open(TRAFFIC_FILE).read()
+        text = open(path).read()
     except OSError:
         return None
     vals = {}
@@ -84,7 +86,7 @@ def recorded_traffic_per_site():
             vals["hash"] = line.split(":", 1)[1].strip()
         if line.startswith("dram_bytes_per_site:"):
             vals["bytes"] = float(line.split(":", 1)[1].strip())
-    if vals.get("hash") != kernel_hash() or "bytes" not in vals:
+    if vals.get("hash") != kernel_hash(sources) or "bytes" not in vals:
         return None
     return vals["bytes"]
 
@@ -221,7 +223,7 @@ def run_blocks(args, rank, world, local):
     D = torch.from_numpy(D_h).cuda()
     C = torch.zeros(n_sets, n_t, dtype=torch.complex128, device="cuda")
     ctx = Context(local)
-    plan = ctx.block_plan(args.op)
+    plan = ctx.block_plan(args.op, args.prec)
     info = plan.info
 
     def step():
@@ -251,7 +253,9 @@ def run_blocks(args, rank, world, local):
     sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
     flops = info["block_flops_per_site"] * n_sites + info["tree_flops_per_slice"] * n_sets * n_t
     achieved = flops / (ms * 1e-3) / 1e12
-    peak = fp64_peak_tflops(sm_max)
+    peak = fp64_peak_tflops(sm_max) if args.prec == "fp64" else fp32_peak_tflops(sm_max)
+    headline_shape = (args.op == OPERATOR and (Lb, Tb) == (L, T) and args.slices <= 0 and args.sets == 1)
+    tps = recorded_traffic_per_site(BLOCK_TRAFFIC_FILE, BLOCK_SOURCES) if headline_shape else None
     # end to end: pinned host fields copied in, C copied out, inside the timed region
     U_pin = torch.from_numpy(U_h).pin_memory()
     D_pin = torch.from_numpy(D_h).pin_memory()
@@ -266,24 +270,28 @@ def run_blocks(args, rank, world, local):
     e2e_s = time.perf_counter() - t0
     if rank == 0:
         line = {"metric": f"sink-site contractions/sec ({args.op} block form, zero-momentum projected blocks, "
-                          f"{Lb}^3x{Tb}, fp64)",
+                          f"{Lb}^3x{Tb}, {args.prec})",
                 "value": world * n_sites / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32x2" if args.prec == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": f"{args.op} {Lb}^3x{Tb}" + (f" ({n_t} slices)" if n_t != Tb else "") +
-                                       f", {n_sets} source(s) per GPU, block form (every baryon projected to p = 0)",
+                                       f", {n_sets} source(s) per GPU, block form (every baryon projected to p = 0)"
+                                       f", {args.prec}",
                            "sites_per_gpu": n_sites,
                            "l2": f"inputs {2 * U_h.nbytes / 1e9:.2f} GB per GPU" +
                                  (", larger than L2" if 2 * U_h.nbytes > 129e6 else ", smaller than L2"),
                            "block_plan": {k: info[k] for k in ("n_w", "expanded_terms", "merged_terms", "factors",
                                                                "level_nodes")}},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None,
+                             "frac": achieved / peak, "traffic": None if tps is None else tps * n_sites,
                              "kernel": "block_project_kernel + block_tree_kernel",
+                             "kernel_source_hash": kernel_hash(BLOCK_SOURCES),
                              "flops_per_site": info["block_flops_per_site"],
                              "tree_flops_per_slice": info["tree_flops_per_slice"],
-                             "peak_basis": f"FP64: {SM_COUNT} SMs x {FP64_FMA_PER_SM} DFMA/cycle x 2 x {sm_max:.0f} MHz "
-                                           "(derived)"},
+                             "peak_basis": (f"FP64: {SM_COUNT} SMs x {FP64_FMA_PER_SM} DFMA/cycle x 2 x {sm_max:.0f} MHz "
+                                            "(derived)" if args.prec == "fp64" else
+                                            f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
+                                            "(derived)")},
                 "cpu_baseline": None,
                 "e2e": {"value": world * n_sites / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(2 * U_h.nbytes),
                         "d2h_bytes_per_step": int(C_pin.numel() * 16)},

@@ -293,7 +293,9 @@ mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, const void* D, 
  *     C[s][t] = sum_k w_k prod_i F^{h_ik}[s][t](eta_ik)
  * with every sink baryon projected to momentum p (p, U, D, C as above; C device complex
  * double [n_sets][T], written): the paper's block setting.  On an L = 1 lattice it
- * equals the local-sink correlator of mbc_correlator.  prec must be MBC_PREC_FP64.
+ * equals the local-sink correlator of mbc_correlator.  prec: MBC_PREC_FP64 (complex
+ * double throughout) or MBC_PREC_MIXED (the projected blocks in double-float
+ * arithmetic with power-of-two site scaling, the factor tree in complex double).
  * ---------------------------------------------------------------------------------- */
 #define MBC_BLOCK_ENTRIES 6912
 typedef enum {

@@ -166,6 +166,186 @@ __global__ void __launch_bounds__(kThreads) block_project_kernel(BlockDev b, con
     for (int f = threadIdx.x; f < nf; f += blockDim.x) o[f] = acc[f];
 }
 
+// ---------------------------------------------------------------- double-float blocks
+// The same projection in double-float arithmetic (complex FP32 pairs, error-free
+// products and sums).  Each site's propagators are scaled by exact powers of two 2^-e
+// (e from the exponent bits of the block's largest |re|, |im|) before the split into
+// (hi, lo) floats, so the block values are of order one; a block entry then carries the
+// factor 2^(2 e_q1 + e_q2).  Every tile first finds the largest such exponent over its
+// sites, per q1 flavour, and adds each site's values times 2^(exponent - largest) (an
+// exact power of two <= 1), so nothing overflows; the tile's sums are converted to
+// double and rescaled once.  The G matrices of the library's block types have entries
+// in {0, +1, -1} (Dirac basis), which the diquark step uses as signs.
+__device__ __forceinline__ unsigned abs_hiword(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+// frexp exponent of a double whose |x| has high word m (0 for x = 0)
+__device__ __forceinline__ int exponent_of(unsigned m) { return m ? (int)(m >> 20) - 1022 : 0; }
+// exact 2^k in double for |k| <= 1022
+__device__ __forceinline__ double pow2d(int k) { return __hiloint2double((1023 + k) << 20, 0); }
+// exact 2^k in float for -126 <= k <= 0, 0 below
+__device__ __forceinline__ float pow2f_le0(int k) { return k < -126 ? 0.f : __int_as_float((127 + k) << 23); }
+
+// max over the block of two unsigned values; red: 64 unsigned of shared scratch
+__device__ __forceinline__ void block_max_u2(unsigned& a, unsigned& b, unsigned* red) {
+    a = __reduce_max_sync(0xffffffffu, a);
+    b = __reduce_max_sync(0xffffffffu, b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { red[warp] = a; red[32 + warp] = b; }
+    __syncthreads();
+    a = 0u;
+    b = 0u;
+    for (int w = 0; w < nw; ++w) { a = max(a, red[w]); b = max(b, red[32 + w]); }
+    __syncthreads();
+}
+
+// U_x, D_x scaled and split (one value per thread: needs blockDim >= 288); returns their
+// exponents
+__device__ __forceinline__ void stage_site_df(const double* __restrict__ U, const double* __restrict__ D,
+                                              int64_t site, cdf* q, unsigned* red, int& eU, int& eD) {
+    const int i = threadIdx.x;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < 144) v = __ldg(reinterpret_cast<const double2*>(U + site * 288) + i);
+    else if (i < 288) v = __ldg(reinterpret_cast<const double2*>(D + site * 288) + (i - 144));
+    const unsigned m = max(abs_hiword(v.x), abs_hiword(v.y));
+    unsigned mu = i < 144 ? m : 0u, md = (i >= 144 && i < 288) ? m : 0u;
+    block_max_u2(mu, md, red);
+    eU = exponent_of(mu);
+    eD = exponent_of(md);
+    if (i < 288) {
+        const double sc = pow2d(-(i < 144 ? eU : eD));
+        cdf z;
+        z.re = df_from_double(v.x * sc);
+        z.im = df_from_double(v.y * sc);
+        q[i] = z;
+    }
+}
+
+__device__ __forceinline__ void diquarks_df(int n_types, const BlockTypeDev* types, const cdf* q, cdf* dq) {
+    for (int e = threadIdx.x; e < n_types * kDq; e += blockDim.x) {
+        const int t = e / kDq, r = e - t * kDq;
+        const int c = r / 144, s = (r / 12) % 12, s2 = r % 12;
+        const BlockTypeDev& ty = types[t];
+        const cdf* q1 = q + ty.q1 * kQ;
+        const cdf* q2 = q + (1 - ty.q1) * kQ;
+        const int a0 = (c + 1) % 3, b0 = (c + 2) % 3;
+        MIXED::A acc;
+        MIXED::acc_zero(acc);
+        for (int k = 0; k < ty.n; ++k) {
+            const int rb = 3 * ty.be[k], rg = 3 * ty.ga[k];
+            // + g Q1[(rb + a0), s] Q2[(rg + b0), s2] - g Q1[(rb + b0), s] Q2[(rg + a0), s2], g = +-1
+            if (ty.g_re[k] > 0.0) {
+                MIXED::fma(acc, q1[(rb + a0) * 12 + s], q2[(rg + b0) * 12 + s2]);
+                MIXED::fms(acc, q1[(rb + b0) * 12 + s], q2[(rg + a0) * 12 + s2]);
+            } else {
+                MIXED::fms(acc, q1[(rb + a0) * 12 + s], q2[(rg + b0) * 12 + s2]);
+                MIXED::fma(acc, q1[(rb + b0) * 12 + s], q2[(rg + a0) * 12 + s2]);
+            }
+        }
+        dq[e] = MIXED::get(acc);
+    }
+}
+
+__device__ __forceinline__ cdf block_entry_df(const BlockTypeDev* types, uint32_t code, const cdf* q, const cdf* dq) {
+    const int slot = code >> 16, s1 = (code >> 12) & 15, s2 = (code >> 8) & 15, s3 = (code >> 4) & 15, al = code & 15;
+    const cdf* q1 = q + types[slot].q1 * kQ + 3 * al * 12;
+    const cdf* d = dq + slot * kDq;
+    MIXED::A a;
+    MIXED::acc_zero(a);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        MIXED::fma(a, d[c * 144 + s3 * 12 + s2], q1[c * 12 + s1]);
+        MIXED::fms(a, d[c * 144 + s1 * 12 + s2], q1[c * 12 + s3]);
+    }
+    return MIXED::get(a);
+}
+
+// unit = (slice, tile, entry chunk); part [slice][tile][n_f] in complex double
+__global__ void __launch_bounds__(kThreads) block_project_df_kernel(BlockDev b, const double* __restrict__ U,
+                                                                     const double* __restrict__ D, int64_t V3, int L,
+                                                                     int px, int py, int pz, int tiles, int f_chunk,
+                                                                     int n_fc, cd* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockTypeDev ty[6];
+    __shared__ unsigned red[64];
+    __shared__ int eref[2];
+    __shared__ cdf ph_s;
+    cdf* q = reinterpret_cast<cdf*>(smem_raw);
+    cdf* dq = q + 2 * kQ;
+    cdf* acc = dq + b.n_types * kDq;
+    load_types(b, ty);
+    const int64_t unit = blockIdx.x;
+    const int fc = (int)(unit % n_fc);
+    const int tile = (int)((unit / n_fc) % tiles);
+    const int64_t slice = unit / ((int64_t)n_fc * tiles);
+    const int f0 = fc * f_chunk;
+    const int nf = min(f_chunk, b.n_f - f0);
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) acc[f] = MIXED::zero();
+    const int64_t x0 = V3 * tile / tiles, x1 = V3 * (tile + 1) / tiles;
+    // largest 2 e_q1 + e_q2 over the tile's sites, for q1 = u and q1 = d (one warp per site)
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        int r0 = -(1 << 30), r1 = -(1 << 30);
+        for (int64_t x = x0 + warp; x < x1; x += nw) {
+            const double2* u = reinterpret_cast<const double2*>(U + (slice * V3 + x) * 288);
+            const double2* d = reinterpret_cast<const double2*>(D + (slice * V3 + x) * 288);
+            unsigned mu = 0u, md = 0u;
+            for (int i = lane; i < 144; i += 32) {
+                const double2 a = __ldg(u + i), c = __ldg(d + i);
+                mu = max(mu, max(abs_hiword(a.x), abs_hiword(a.y)));
+                md = max(md, max(abs_hiword(c.x), abs_hiword(c.y)));
+            }
+            mu = __reduce_max_sync(0xffffffffu, mu);
+            md = __reduce_max_sync(0xffffffffu, md);
+            const int eu = exponent_of(mu), ed = exponent_of(md);
+            r0 = max(r0, 2 * eu + ed);
+            r1 = max(r1, 2 * ed + eu);
+        }
+        if (lane == 0) { red[warp] = (unsigned)(r0 + (1 << 30)); red[32 + warp] = (unsigned)(r1 + (1 << 30)); }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned m0 = 0u, m1 = 0u;
+            for (int w = 0; w < nw; ++w) { m0 = max(m0, red[w]); m1 = max(m1, red[32 + w]); }
+            eref[0] = (int)m0 - (1 << 30);
+            eref[1] = (int)m1 - (1 << 30);
+        }
+        __syncthreads();
+    }
+    const bool mom = (px | py | pz) != 0;
+    for (int64_t x = x0; x < x1; ++x) {
+        __syncthreads();
+        int eU, eD;
+        stage_site_df(U, D, slice * V3 + x, q, red, eU, eD);
+        if (mom && threadIdx.x == 0) {
+            const int64_t cx = x % L, cy = (x / L) % L, cz = x / ((int64_t)L * L);
+            int64_t k = ((int64_t)px * cx + (int64_t)py * cy + (int64_t)pz * cz) % L;
+            if (k < 0) k += L;
+            double sn, cs;
+            sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
+            ph_s.re = df_from_double(cs);
+            ph_s.im = df_from_double(sn);
+        }
+        __syncthreads();
+        diquarks_df(b.n_types, ty, q, dq);
+        __syncthreads();
+        const float sc0 = pow2f_le0(2 * eU + eD - eref[0]), sc1 = pow2f_le0(2 * eD + eU - eref[1]);
+        const cdf ph = ph_s;
+        for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+            const uint32_t code = entry_code(b, f0 + f);
+            cdf v = block_entry_df(ty, code, q, dq);
+            if (mom) v = MIXED::mul(v, ph);
+            const float sc = ty[code >> 16].q1 ? sc1 : sc0;
+            v.re.hi *= sc; v.re.lo *= sc; v.im.hi *= sc; v.im.lo *= sc;
+            acc[f] = MIXED::vadd(acc[f], v);
+        }
+    }
+    cd* o = part + (slice * tiles + tile) * (int64_t)b.n_f + f0;
+    const double s0 = pow2d(max(min(eref[0], 1000), -1000)), s1 = pow2d(max(min(eref[1], 1000), -1000));
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+        const cdf v = acc[f];
+        const double sc = ty[entry_code(b, f0 + f) >> 16].q1 ? s1 : s0;
+        o[f] = cd_make(df_to_double(v.re) * sc, df_to_double(v.im) * sc);
+    }
+}
+
 // F[slice][f] = sum over tiles in order (compensated)
 __global__ void block_tile_reduce_kernel(const cd* __restrict__ part, int64_t n_slices, int tiles, int n_f,
                                          cd* __restrict__ F) {
@@ -260,7 +440,7 @@ cudaError_t launch_blocks_site(const BlockDev& b, const double* U, const double*
     return cudaGetLastError();
 }
 
-cudaError_t launch_blocks_projected(const BlockDev& b, const double* U, const double* D, int64_t n_slices,
+cudaError_t launch_blocks_projected(const BlockDev& b, int prec, const double* U, const double* D, int64_t n_slices,
                                     int64_t V3, int L, const int* p, cd* part, cd* F, int sms, cudaStream_t s,
                                     int64_t* launches) {
     if (n_slices <= 0 || b.n_f <= 0) return cudaSuccess;
@@ -268,12 +448,20 @@ cudaError_t launch_blocks_projected(const BlockDev& b, const double* U, const do
     int f_chunk, n_fc, tiles;
     project_shape(b.n_f, b.n_types, n_slices, V3, sms, f_chunk, n_fc, tiles);
     const size_t smem = block_kernel_smem(f_chunk, b.n_types, true);
-    cudaError_t e = cudaFuncSetAttribute(block_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int64_t units = n_slices * tiles * n_fc;
     const int px = p ? p[0] : 0, py = p ? p[1] : 0, pz = p ? p[2] : 0;
-    block_project_kernel<<<(unsigned)units, kThreads, smem, s>>>(b, U, D, V3, L, px, py, pz, tiles, f_chunk, n_fc,
-                                                                 part);
+    if (prec == 0) {
+        cudaError_t e = cudaFuncSetAttribute(block_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        block_project_kernel<<<(unsigned)units, kThreads, smem, s>>>(b, U, D, V3, L, px, py, pz, tiles, f_chunk, n_fc,
+                                                                     part);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(block_project_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        block_project_df_kernel<<<(unsigned)units, kThreads, smem, s>>>(b, U, D, V3, L, px, py, pz, tiles, f_chunk,
+                                                                        n_fc, part);
+    }
     ++*launches;
     const int64_t n = n_slices * b.n_f;
     block_tile_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, n_slices, tiles, b.n_f, F);

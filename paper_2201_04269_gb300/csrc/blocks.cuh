@@ -46,9 +46,11 @@ size_t block_kernel_smem(int n_f, int n_types, bool projected);
 cudaError_t launch_blocks_site(const BlockDev& b, const double* U, const double* D, int64_t n_sites, cd* out,
                                int sms, cudaStream_t s, int64_t* launches);
 // Projected blocks: F [n_slices][b.n_f] = sum over the V3 sites of each slice of
-// e^{-i 2 pi p.x / L} f(x); part: scratch of block_project_scratch(...) complex doubles.
+// e^{-i 2 pi p.x / L} f(x), in complex double (prec 0) or double-float (prec 1, block
+// types with G entries in {0, +1, -1}); part: scratch of block_project_scratch(...)
+// complex doubles.
 int64_t block_project_scratch(int n_f, int n_types, int64_t n_slices, int64_t V3, int sms);
-cudaError_t launch_blocks_projected(const BlockDev& b, const double* U, const double* D, int64_t n_slices,
+cudaError_t launch_blocks_projected(const BlockDev& b, int prec, const double* U, const double* D, int64_t n_slices,
                                     int64_t V3, int L, const int* p, cd* part, cd* F, int sms, cudaStream_t s,
                                     int64_t* launches);
 // Factor tree over projected blocks: part [n_slices][t.n_chunks] compensated partial sums.

@@ -52,8 +52,8 @@ mbc_status check_fields(mbc_ctx* c, const void* U, const void* D, int64_t n_site
 
 // projected blocks of b into F (n_slices x b.n_f complex double; NULL = the context's
 // buffer), with the tile partials in the context's pool
-mbc_status project(mbc_ctx* c, const BlockDev& b, const void* U, const void* D, int64_t n_slices, int64_t V3, int L,
-                   const int* p, void* F, cudaStream_t s) {
+mbc_status project(mbc_ctx* c, const BlockDev& b, int prec, const void* U, const void* D, int64_t n_slices, int64_t V3,
+                   int L, const int* p, void* F, cudaStream_t s) {
     const int64_t nscr = block_project_scratch(b.n_f, b.n_types, n_slices, V3, c->sms);
     mbc_status st = ensure(c, c->blk_part, sizeof(cd) * (size_t)std::max<int64_t>(nscr, 1), s);
     if (st != MBC_OK) return st;
@@ -62,7 +62,7 @@ mbc_status project(mbc_ctx* c, const BlockDev& b, const void* U, const void* D, 
         if (st != MBC_OK) return st;
         F = c->blk_F.p;
     }
-    cudaError_t e = launch_blocks_projected(b, (const double*)U, (const double*)D, n_slices, V3, L, p, (cd*)c->blk_part.p,
+    cudaError_t e = launch_blocks_projected(b, prec, (const double*)U, (const double*)D, n_slices, V3, L, p, (cd*)c->blk_part.p,
                                             (cd*)F, c->sms, s, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "projected block launch");
     return MBC_OK;
@@ -125,7 +125,7 @@ mbc_status mbc_hadron_blocks_projected(mbc_ctx* c, int type, const void* U, cons
     fill_types(b, std::vector<int>{type});
     cudaStream_t s = (cudaStream_t)stream;
     if (n_slices > 0) {
-        st = project(c, b, U, D, n_slices, V3, L, p, F, s);
+        st = project(c, b, MBC_PREC_FP64, U, D, n_slices, V3, L, p, F, s);
         if (st != MBC_OK) return st;
     }
     c->err.clear();
@@ -136,7 +136,7 @@ mbc_status mbc_block_plan_create(mbc_ctx* c, int op, int prec, mbc_block_plan** 
     if (!c || !out) return MBC_INVALID_ARG;
     *out = nullptr;
     if (op < 0 || op > MBC_OP_HE3_II_S) return fail(c, MBC_INVALID_ARG, "unknown operator");
-    if (prec != MBC_PREC_FP64) return fail(c, MBC_UNSUPPORTED, "block plans evaluate in MBC_PREC_FP64 only");
+    if (prec != MBC_PREC_FP64 && prec != MBC_PREC_MIXED) return fail(c, MBC_INVALID_ARG, "unknown precision");
     mbc_block_plan* P = new (std::nothrow) mbc_block_plan();
     if (!P) return fail(c, MBC_OOM, "host allocation failed");
     P->ctx = c;
@@ -279,7 +279,7 @@ mbc_status mbc_block_correlator(mbc_block_plan* P, const void* U, const void* D,
         c->err.clear();
         return MBC_OK;
     }
-    st = project(c, P->bd, U, D, n_slices, V3, L, p, nullptr, s);
+    st = project(c, P->bd, P->hp.prec, U, D, n_slices, V3, L, p, nullptr, s);
     if (st != MBC_OK) return st;
     st = ensure(c, c->blk_tree, sizeof(d4) * (size_t)(n_slices * P->td.n_chunks), s);
     if (st != MBC_OK) return st;

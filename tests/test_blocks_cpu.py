@@ -60,8 +60,9 @@ def test_block_argument_errors(abi, hctx):
         abi.mbc_block_plan_create(hctx, "no_such_operator")
     assert e.value.status == 1
     with pytest.raises(abi.MbcError) as e:
-        abi.mbc_block_plan_create(hctx, "proton", "mixed")
-    assert e.value.status == 2
+        abi.mbc_block_plan_create(hctx, "proton", "no_such_precision")
+    assert e.value.status == 1
+    abi.mbc_block_plan_destroy(abi.mbc_block_plan_create(hctx, "proton", "mixed"))
     # a host-only context cannot evaluate (checked before any pointer is used)
     with pytest.raises(abi.MbcError) as e:
         abi.mbc_hadron_blocks(hctx, "P", 1, 1, 1, 1)

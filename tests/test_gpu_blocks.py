@@ -79,6 +79,46 @@ def test_block_correlator_matches_oracle(ctx, name, wl, L, T, p):
     plan.destroy()
 
 
+@pytest.mark.parametrize("name,wl,L,T,p", [("proton", "proton_4x8", 4, 3, (1, 2, 0)),
+                                           ("dinucleon_I", "dinucleon_16x32", 3, 2, (0, 1, 1)),
+                                           ("he3_I", "he3_24x48", 2, 2, None)])
+def test_mixed_block_correlator_matches_oracle(ctx, name, wl, L, T, p):
+    """Double-float projected blocks: within the mixed tolerance 1e-5 and, by design
+    (about 2^-46 per operation), within 1e-9."""
+    U, D = fields(wl, L=L, T=T)
+    ref = obl.BlockPlan(name, "canonical")
+    want = obl.correlator_projected(ref, U, D, L, p or (0, 0, 0))
+    plan = ctx.block_plan(name, "mixed")
+    C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    plan.correlator(dev(U[None]), dev(D[None]), C, L, p)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()[0]
+    assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-9
+    plan.destroy()
+
+
+def test_mixed_block_correlator_wide_exponent_range(ctx):
+    """Sites of one slice whose propagators differ by 2^40 in scale (and slices at
+    exp(-0.5 t) down to t = 47): the per-site power-of-two scaling keeps the double-float
+    projection accurate."""
+    L, T = 3, 2
+    U, D = fields("he3_24x48", L=L, t_list=[0, 47])
+    s = np.ones(L ** 3)
+    s[::5] = 2.0 ** 20
+    s[1::7] = 2.0 ** -20
+    U = U * s[None, :, None, None]
+    D = D * s[None, :, None, None]
+    ref = obl.BlockPlan("he3_I", "canonical")
+    want = obl.correlator_projected(ref, U, D, L)
+    plan = ctx.block_plan("he3_I", "mixed")
+    C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    plan.correlator(dev(U[None]), dev(D[None]), C, L)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()[0]
+    assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-9
+    plan.destroy()
+
+
 def test_he3_II_s_block_correlator_ragged_lattice(ctx):
     """3He_II-s on 5^3 x 2: several tiles per slice with a ragged last tile."""
     L, T = 5, 2
