@@ -85,16 +85,17 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
             P::acc_zero(acc);
             const int e1 = __ldg(d.g_off + b * NJ + j + 1);
             for (int e = __ldg(d.g_off + b * NJ + j); e < e1; ++e) P::fma_s(acc, __ldg(gws + e), T[__ldg(d.g_a + e)]);
-            g[j] = P::get(acc);
+            g[j] = P::get_s(acc);
         }
         for (int pr = p0; pr < p1; ++pr) {
+            // K(C_b, R_b) (+)= sum_j coef_j G_j, accumulated onto the stored value
+            V* kp = K + (size_t)__ldg(d.pair_b + pr) * n_rb + b;
             typename P::A h;
-            P::acc_zero(h);
+            if (__ldg(d.pair_first + pr)) P::acc_zero(h);
+            else P::acc_set(h, *kp);
 #pragma unroll
             for (int j = 0; j < NJ; ++j) P::fma_s(h, __ldg(pcs + pr * NJ + j), g[j]);
-            V* kp = K + (size_t)__ldg(d.pair_b + pr) * n_rb + b;
-            const V hv = P::get(h);
-            *kp = __ldg(d.pair_first + pr) ? hv : P::vadd(*kp, hv);
+            *kp = P::get_s(h);
         }
     }
 }
