@@ -296,9 +296,11 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
     auto it = ctx->tune_cache.find(P->signature);
     if (it != ctx->tune_cache.end()) P->sched = it->second;
     else if (h.algo == MBC_ALGO_EGRAPH) {
-        // 384 threads (12 warps) per block, as many blocks per SM as shared memory and
-        // the 2048-thread limit allow
-        P->sched.threads = 384;
+        // 384 threads (12 warps) per block, or the B row-set count rounded up to whole warps
+        // when that lies in 257..384 (one row set per thread in the leaf stage, no idle
+        // warp), as many blocks per SM as shared memory and the 2048-thread limit allow
+        const int rows_w = (P->ed.n_rows_b + 31) / 32 * 32;
+        P->sched.threads = (rows_w > 256 && rows_w <= 384) ? rows_w : 384;
         const int by_smem = (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024));
         P->sched.blocks_per_sm = std::max(1, std::min(by_smem, 2048 / P->sched.threads));
     }
