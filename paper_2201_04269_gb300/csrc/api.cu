@@ -158,8 +158,12 @@ mbc_status upload(mbc_plan* P) {
         for (int k = 0; k < 7; ++k) {
             mo[w].child[k] = b.add(m.child[k]);
             mo[w].row[k] = b.add(m.row[k]);
+            // transposed: word i of entry e at [i * n + e]
             std::vector<uint32_t> pk(m.child[k].size());
-            for (size_t i = 0; i < pk.size(); ++i) pk[i] = (uint32_t)m.child[k][i] | ((uint32_t)m.row[k][i] << 16);
+            const size_t n = k ? pk.size() / k : 0;
+            for (size_t e = 0; e < n; ++e)
+                for (int i = 0; i < k; ++i)
+                    pk[i * n + e] = (uint32_t)m.child[k][e * k + i] | ((uint32_t)m.row[k][e * k + i] << 16);
             mo[w].pack[k] = b.add(pk);
         }
         std::vector<uint8_t> lev, col;
@@ -181,6 +185,36 @@ mbc_status upload(mbc_plan* P) {
         for (auto& x : e.pair_coef) { pcf.push_back((float)x.real()); pcd.push_back(x.real()); }
     }
     size_t o_gp = pr == 0 ? b.add(gwd) : b.add(gwf), o_pcf = pr == 0 ? b.add(pcd) : b.add(pcf);
+    // sliced-ELL copy of the G entries (slices of 32 B row sets; weights exact in float)
+    std::vector<int2> sell;
+    std::vector<int32_t> sell_off, sell_w;
+    {
+        const int nrb = e.B.n ? (int)e.B.level_rows[e.B.n].size() : 1, nj = e.n_j;
+        const int n_slices = (nrb + 31) / 32;
+        if (compact && nj > 0 && (int)e.g_off.size() == nrb * nj + 1)
+            for (int sl = 0; sl < n_slices; ++sl)
+                for (int j = 0; j < nj; ++j) {
+                    int width = 0;
+                    for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
+                        const int it = (sl * 32 + l) * nj + j;
+                        width = std::max(width, e.g_off[it + 1] - e.g_off[it]);
+                    }
+                    sell_off.push_back((int32_t)sell.size());
+                    sell_w.push_back(width);
+                    const size_t base = sell.size();
+                    sell.resize(base + (size_t)width * 32, int2{0, 0});
+                    for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
+                        const int it = (sl * 32 + l) * nj + j;
+                        for (int k = 0; k < e.g_off[it + 1] - e.g_off[it]; ++k) {
+                            const float wf = (float)e.g_w[e.g_off[it] + k].real();
+                            int bits;
+                            std::memcpy(&bits, &wf, 4);
+                            sell[base + (size_t)k * 32 + l] = int2{e.g_a[e.g_off[it] + k], bits};
+                        }
+                    }
+                }
+    }
+    size_t o_sell = b.add(sell), o_soff = b.add(sell_off), o_sellw = b.add(sell_w);
 
     void* dev = nullptr;
     cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
@@ -239,6 +273,7 @@ mbc_status upload(mbc_plan* P) {
     ed.g_off = at<int32_t>(dev, o_goff); ed.g_a = at<int32_t>(dev, o_ga); ed.g_w = at<Val16>(dev, o_gw);
     ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_first = at<uint8_t>(dev, o_pf);
     ed.pair_coef = at<Val16>(dev, o_pc);
+    ed.sell = at<int2>(dev, o_sell); ed.sell_off = at<int32_t>(dev, o_soff); ed.sell_w = at<int32_t>(dev, o_sellw);
     // levels 0..n-1 plus two buffers for the leaf level; G only for the general leaf path
     ed.stack_a = ed.A.off[ed.A.n] + 2 * ed.A.size[ed.A.n];
     ed.stack_b = ed.B.off[ed.B.n] + 2 * ed.B.size[ed.B.n];

@@ -69,7 +69,8 @@ struct MinorDev {
     int off[7];                    // offset of level k in a stacked table
     const uint16_t* child[7];      // [e * k + i]
     const uint8_t* row[7];
-    const uint32_t* pack[7];       // [e * k + i] = child | row << 16
+    const uint32_t* pack[7];       // [i * size[k] + e] = child | row << 16 (one entry's words strided,
+                                   // so the threads of a warp read consecutive words)
     int n_nodes;
     const uint8_t* node_level;
     const uint8_t* node_col;
@@ -92,6 +93,13 @@ struct EgraphDev {
     int stack_b;                     // values in the B stack (levels 0..n_B)
     int smem_values;                 // total complex values in dynamic shared memory
     int stage_pk;                    // copy the leaf-level packed tables to shared memory
+    // G entries of the fused leaf path in sliced-ELL form: for the 32 B row sets of slice
+    // s and free index j, entry k of lane l at sell[sell_off[s * n_j + j] + k * 32 + l]
+    // (k < sell_w[s * n_j + j]; padding entries have weight 0), so the loads of a warp are
+    // consecutive 8-byte records
+    const int2* sell;                // (T index, float weight bits)
+    const int32_t* sell_off;
+    const int32_t* sell_w;
 };
 
 // One item of a batched launch: a plan's device view, its fields, where its per-site

@@ -35,7 +35,7 @@ __device__ __forceinline__ void laplace_k(const MinorDev& m, const uint32_t* pk,
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         uint32_t w[K];
 #pragma unroll
-        for (int i = 0; i < K; ++i) w[i] = pk[e * K + i];
+        for (int i = 0; i < K; ++i) w[i] = pk[i * n + e];
         typename P::A acc;
         P::acc_zero(acc);
 #pragma unroll
@@ -73,18 +73,31 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
                                            typename P::V* __restrict__ K) {
     typedef typename P::V V;
     typedef typename P::S S;
-    const S* gws = reinterpret_cast<const S*>(d.g_ws);
     const S* pcs = reinterpret_cast<const S*>(d.pair_cs);
     const int n_rb = d.n_rows_b;
     const int p0 = __ldg(d.pair_off + leaf), p1 = __ldg(d.pair_off + leaf + 1);
+    const int lane = threadIdx.x & 31;
     for (int b = threadIdx.x; b < n_rb; b += blockDim.x) {
         V g[NJ];
+        const int sl = b >> 5;      // slice of 32 row sets (blockDim is a multiple of 32)
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             typename P::A acc;
             P::acc_zero(acc);
-            const int e1 = __ldg(d.g_off + b * NJ + j + 1);
-            for (int e = __ldg(d.g_off + b * NJ + j); e < e1; ++e) P::fma_s(acc, __ldg(gws + e), T[__ldg(d.g_a + e)]);
+            if (P::kind == 1) {
+                // double-float: issue-bound, coalesced sliced-ELL records (padding is cheap)
+                const int2* ent = d.sell + __ldg(d.sell_off + sl * NJ + j) + lane;
+                const int width = __ldg(d.sell_w + sl * NJ + j);
+                for (int k = 0; k < width; ++k) {
+                    const int2 r = __ldg(ent + k * 32);
+                    P::fma_s(acc, (S)__int_as_float(r.y), T[r.x]);
+                }
+            } else {
+                // FP64: bound by the FP64 pipe, so no padded entries (row-wise lists)
+                const S* gws = reinterpret_cast<const S*>(d.g_ws);
+                const int e1 = __ldg(d.g_off + b * NJ + j + 1);
+                for (int e = __ldg(d.g_off + b * NJ + j); e < e1; ++e) P::fma_s(acc, __ldg(gws + e), T[__ldg(d.g_a + e)]);
+            }
             g[j] = P::get_s(acc);
         }
         for (int pr = p0; pr < p1; ++pr) {

@@ -180,12 +180,15 @@ struct MIXED {
     __device__ __forceinline__ static void fma_s(A& a, S w, V x) { dacc_fma_f(a.r0, w, x.re); dacc_fma_f(a.i0, w, x.im); }
     __device__ __forceinline__ static V vadd(V a, V b) { V r; r.re = df_add(a.re, b.re); r.im = df_add(a.im, b.im); return r; }
     // accumulator that starts from a value (chains r0, i0); get_s reads an accumulator fed
-    // only by acc_set and fma_s, which leave r1, i1 at zero
+    // only by acc_set and fma_s, which leave r1, i1 at zero, as an unnormalised pair
+    // (hi + lo with |lo| small: every double-float operation here accepts that form)
     __device__ __forceinline__ static void acc_set(A& a, V x) {
         a.r0.hi = x.re.hi; a.r0.lo = x.re.lo; a.i0.hi = x.im.hi; a.i0.lo = x.im.lo;
         dacc_zero(a.r1); dacc_zero(a.i1);
     }
-    __device__ __forceinline__ static V get_s(const A& a) { V v; v.re = dacc_get(a.r0); v.im = dacc_get(a.i0); return v; }
+    __device__ __forceinline__ static V get_s(const A& a) {
+        V v; v.re.hi = a.r0.hi; v.re.lo = a.r0.lo; v.im.hi = a.i0.hi; v.im.lo = a.i0.lo; return v;
+    }
     __device__ __forceinline__ static V get(const A& a) {
         V v;
         v.re = df_add(dacc_get(a.r0), dacc_get(a.r1));
