@@ -215,6 +215,17 @@ mbc_status upload(mbc_plan* P) {
                 }
     }
     size_t o_sell = b.add(sell), o_soff = b.add(sell_off), o_sellw = b.add(sell_w);
+    std::vector<int4> prec_;
+    if (compact && e.n_j >= 1 && e.n_j <= 2)
+        for (size_t q = 0; q < e.pair_b.size(); ++q) {
+            int4 r{e.pair_b[q] | (e.pair_first[q] ? (int)0x80000000u : 0), 0, 0, 0};
+            const float c0 = (float)e.pair_coef[q * e.n_j].real();
+            const float c1 = (float)e.pair_coef[q * e.n_j + e.n_j - 1].real();
+            std::memcpy(&r.y, &c0, 4);
+            std::memcpy(&r.z, &c1, 4);
+            prec_.push_back(r);
+        }
+    size_t o_prec = b.add(prec_);
 
     void* dev = nullptr;
     cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
@@ -274,6 +285,7 @@ mbc_status upload(mbc_plan* P) {
     ed.pair_off = at<int32_t>(dev, o_poff); ed.pair_b = at<int32_t>(dev, o_pb); ed.pair_first = at<uint8_t>(dev, o_pf);
     ed.pair_coef = at<Val16>(dev, o_pc);
     ed.sell = at<int2>(dev, o_sell); ed.sell_off = at<int32_t>(dev, o_soff); ed.sell_w = at<int32_t>(dev, o_sellw);
+    ed.pair_rec = at<int4>(dev, o_prec);
     // levels 0..n-1 plus two buffers for the leaf level; G only for the general leaf path
     ed.stack_a = ed.A.off[ed.A.n] + 2 * ed.A.size[ed.A.n];
     ed.stack_b = ed.B.off[ed.B.n] + 2 * ed.B.size[ed.B.n];

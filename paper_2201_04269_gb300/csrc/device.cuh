@@ -100,6 +100,9 @@ struct EgraphDev {
     const int2* sell;                // (T index, float weight bits)
     const int32_t* sell_off;
     const int32_t* sell_w;
+    // pairs of the fused leaf path (n_j <= 2, weights exact in float): (B column |
+    // first update << 31, float bits of coef_0, of coef_1, 0)
+    const int4* pair_rec;
 };
 
 // One item of a batched launch: a plan's device view, its fields, where its per-site

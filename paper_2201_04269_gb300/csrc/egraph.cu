@@ -73,7 +73,6 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
                                            typename P::V* __restrict__ K) {
     typedef typename P::V V;
     typedef typename P::S S;
-    const S* pcs = reinterpret_cast<const S*>(d.pair_cs);
     const int n_rb = d.n_rows_b;
     const int p0 = __ldg(d.pair_off + leaf), p1 = __ldg(d.pair_off + leaf + 1);
     const int lane = threadIdx.x & 31;
@@ -100,15 +99,53 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
             }
             g[j] = P::get_s(acc);
         }
-        for (int pr = p0; pr < p1; ++pr) {
-            // K(C_b, R_b) (+)= sum_j coef_j G_j, accumulated onto the stored value
-            V* kp = K + (size_t)__ldg(d.pair_b + pr) * n_rb + b;
-            typename P::A h;
-            if (__ldg(d.pair_first + pr)) P::acc_zero(h);
-            else P::acc_set(h, *kp);
+        // K(C_b, R_b) (+)= sum_j coef_j G_j, accumulated onto the stored value
+        if (P::kind == 1) {
+            // double-float: one 16-byte record per pair (B column | first update << 31,
+            // coef_0, coef_1 as float bits); two pairs at a time (the pairs of one leaf go
+            // to distinct K columns, so both loads may precede both stores)
+            int pr = p0;
+            for (; pr + 1 < p1; pr += 2) {
+                const int4 r0 = __ldg(d.pair_rec + pr), r1 = __ldg(d.pair_rec + pr + 1);
+                V* k0 = K + (size_t)(r0.x & 0x7fffffff) * n_rb + b;
+                V* k1 = K + (size_t)(r1.x & 0x7fffffff) * n_rb + b;
+                const V v0 = r0.x < 0 ? P::zero() : *k0;
+                const V v1 = r1.x < 0 ? P::zero() : *k1;
+                typename P::A h0, h1;
+                P::acc_set(h0, v0);
+                P::acc_set(h1, v1);
+                P::fma_s(h0, (S)__int_as_float(r0.y), g[0]);
+                P::fma_s(h1, (S)__int_as_float(r1.y), g[0]);
+                if (NJ > 1) {
+                    P::fma_s(h0, (S)__int_as_float(r0.z), g[NJ - 1]);
+                    P::fma_s(h1, (S)__int_as_float(r1.z), g[NJ - 1]);
+                }
+                *k0 = P::get_s(h0);
+                *k1 = P::get_s(h1);
+            }
+            if (pr < p1) {
+                const int4 rec = __ldg(d.pair_rec + pr);
+                V* kp = K + (size_t)(rec.x & 0x7fffffff) * n_rb + b;
+                typename P::A h;
+                if (rec.x < 0) P::acc_zero(h);
+                else P::acc_set(h, *kp);
+                P::fma_s(h, (S)__int_as_float(rec.y), g[0]);
+                if (NJ > 1) P::fma_s(h, (S)__int_as_float(rec.z), g[NJ - 1]);
+                *kp = P::get_s(h);
+            }
+        } else {
+            // FP64: coefficients stored as doubles (a float-to-double conversion would take
+            // a slot of the FP64 pipe that bounds this kernel)
+            const S* pcs = reinterpret_cast<const S*>(d.pair_cs);
+            for (int pr = p0; pr < p1; ++pr) {
+                V* kp = K + (size_t)__ldg(d.pair_b + pr) * n_rb + b;
+                typename P::A h;
+                if (__ldg(d.pair_first + pr)) P::acc_zero(h);
+                else P::acc_set(h, *kp);
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) P::fma_s(h, __ldg(pcs + pr * NJ + j), g[j]);
-            *kp = P::get_s(h);
+                for (int j = 0; j < NJ; ++j) P::fma_s(h, __ldg(pcs + pr * NJ + j), g[j]);
+                *kp = P::get_s(h);
+            }
         }
     }
 }
