@@ -321,6 +321,7 @@ def main():
     ap.add_argument("--seed", type=int, default=SEED)
     ap.add_argument("--kappa", type=float, default=KAPPA)
     ap.add_argument("--noise", type=float, default=None)
+    ap.add_argument("--batched", action="store_true", help="also time the batched form (always on the headline)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -437,6 +438,41 @@ def main():
                 "rel_err_mixed_vs_fp64": err}
         p64.destroy()
 
+    # the batched form: the same sites as items of one persistent launch (four time-slice
+    # groups per set, mbc_batch), captured once in a CUDA graph and replayed
+    batched = None
+    if headline or args.batched:
+        from paper_2201_04269_gb300 import abi
+        groups = 4 if n_t >= 4 else 1
+        bounds = [int(round(n_t * k / groups)) for k in range(groups + 1)]
+        items = []
+        for si in range(n_sets):
+            for g0, g1 in zip(bounds[:-1], bounds[1:]):
+                items.append({"plan": plan.handle, "U": U[si, g0:g1], "D": D[si, g0:g1], "n_sets": 1,
+                              "T": g1 - g0, "V3": n_v, "C": C[si, g0:g1]})
+        abi.mbc_batch_reserve(ctx.handle, items)
+        ctx.batch(items, stream=stream)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        l0 = ctx.launches
+        with torch.cuda.graph(graph, stream=cap):
+            ctx.batch(items, stream=torch.cuda.current_stream())
+        per_replay = ctx.launches - l0
+        graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msb = e0.elapsed_time(e1) / args.steps
+        batched = {"value": world * n_sites / (msb * 1e-3), "unit": UNIT, "ms_per_step": msb, "items": len(items),
+                   "cuda_graph": True, "launches_per_step": per_replay,
+                   "matches_single_launch": bool(np.array_equal(C.cpu().numpy()[0], C_mixed))}
+        del graph
+
     # end to end through the host-buffer entry point (pinned host memory)
     U_pin = torch.from_numpy(U_h).pin_memory()
     D_pin = torch.from_numpy(D_h).pin_memory()
@@ -469,7 +505,8 @@ def main():
                            "l2": f"inputs {2 * U_h.nbytes / 1e9:.2f} GB per GPU" +
                                  (", larger than L2" if 2 * U_h.nbytes > 129e6 else ", smaller than L2"),
                            "canonical_terms": info["canonical_terms"], "index_size": info["index_size"]},
-                "roofline": roofline, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "fp64": fp64, "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.destroy()

@@ -795,6 +795,10 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
             if (e != cudaSuccess) return cuda_fail(c, e, "item table upload");
         }
     }
+    // block size: the largest e-graph schedule among the items (a multiple of 32, <= 384)
+    int threads = 32;
+    for (int i = 0; i < n_items; ++i) threads = std::max(threads, items[i].plan->sched.threads);
+    c->batch_threads = std::min(threads, 384);
     c->batch_kslot = kslot;
     c->batch_grid = grid;
     c->batch_reserved.assign(items, items + n_items);
@@ -819,7 +823,8 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
     for (int pr = 0; pr < 2; ++pr) {
         if (c->batch_host[pr].empty()) continue;
         cudaError_t e = launch_egraph_batch((const BatchItem*)c->batch_items.p + (size_t)pr * n_slots,
-                                            (int)c->batch_host[pr].size(), c->batch_units[pr], pr, 384, c->batch_grid,
+                                            (int)c->batch_host[pr].size(), c->batch_units[pr], pr, c->batch_threads,
+                                            c->batch_grid,
                                             c->batch_smem[pr], (unsigned int*)c->counter.p, c->batch_k.p,
                                             c->batch_kslot, s, &c->launches);
         if (e != cudaSuccess) return cuda_fail(c, e, "batched kernel launch");

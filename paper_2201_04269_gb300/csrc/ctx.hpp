@@ -32,7 +32,7 @@ struct mbc_ctx {
     std::vector<mbc::BatchItem> batch_host[2];
     size_t batch_smem[2] = {0, 0};
     int64_t batch_units[2] = {0, 0}, batch_kslot = 0;
-    int batch_grid = 0;
+    int batch_grid = 0, batch_threads = 384;
     // hadron blocks: per-tile partial blocks, projected blocks, tree partials
     mbc::Buf blk_part, blk_F, blk_tree;
 };

@@ -310,9 +310,11 @@ __global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* 
 
 // Several (plan, fields) items in one persistent launch: work units are (item, site),
 // numbered item by item; a block takes units from the counter, finds the item by a
-// search over the unit offsets and evaluates the site with that item's plan.
+// search over the unit offsets and evaluates the site with that item's plan.  Three
+// resident blocks of up to 384 threads per SM: the register cap this implies (56) costs a
+// few spills of the per-item plan view, which the occupancy more than repays.
 template <class P>
-__global__ void __launch_bounds__(384) egraph_batch_kernel(const BatchItem* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(384, 3) egraph_batch_kernel(const BatchItem* __restrict__ items, int n_items,
                                                            int64_t n_units, unsigned int* __restrict__ counter,
                                                            typename P::V* __restrict__ kscratch, int64_t kslot_values) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
