@@ -40,10 +40,11 @@ __device__ __forceinline__ void laplace_k(const MinorDev& m, const uint32_t* pk,
         P::acc_zero(acc);
 #pragma unroll
         for (int i = 0; i < K; ++i) {
+            // the term's sign (-1)^(i+q) goes into the parent value's sign bits, so every
+            // term is one multiply-add
             const typename P::V a = mc[(w[i] >> 16) * kLd];
-            const typename P::V p = parent[w[i] & 0xFFFFu];
-            if (((i & 1) ? -sign : sign) > 0) P::fma(acc, a, p);
-            else P::fms(acc, a, p);
+            const typename P::V p = P::flip(parent[w[i] & 0xFFFFu], (i & 1) ? -sign : sign);
+            P::fma(acc, a, p);
         }
         dest[e] = P::get(acc);
     }

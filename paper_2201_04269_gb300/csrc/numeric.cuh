@@ -137,6 +137,12 @@ struct FP64 {
         return cd_make(__fma_rn(x.re, y.re, -x.im * y.im), __fma_rn(x.re, y.im, x.im * y.re));
     }
     __device__ __forceinline__ static V neg(V x) { return cd_make(-x.re, -x.im); }
+    // x for s > 0, -x otherwise, by the sign bits (integer operations only)
+    __device__ __forceinline__ static V flip(V x, int s) {
+        const long long m = s > 0 ? 0ll : (long long)0x8000000000000000ull;
+        return cd_make(__longlong_as_double(__double_as_longlong(x.re) ^ m),
+                       __longlong_as_double(__double_as_longlong(x.im) ^ m));
+    }
     // Smith's complex division (R. L. Smith, 1962)
     __device__ __forceinline__ static V div(V a, V b) {
         if (fabs(b.re) >= fabs(b.im)) {
@@ -199,6 +205,14 @@ struct MIXED {
         A a; acc_zero(a); fma(a, x, y); return get(a);
     }
     __device__ __forceinline__ static V neg(V x) { V r; r.re = df_neg(x.re); r.im = df_neg(x.im); return r; }
+    // x for s > 0, -x otherwise, by the sign bits (integer operations only)
+    __device__ __forceinline__ static V flip(V x, int s) {
+        const unsigned m = s > 0 ? 0u : 0x80000000u;
+        V r;
+        r.re.hi = __uint_as_float(__float_as_uint(x.re.hi) ^ m); r.re.lo = __uint_as_float(__float_as_uint(x.re.lo) ^ m);
+        r.im.hi = __uint_as_float(__float_as_uint(x.im.hi) ^ m); r.im.lo = __uint_as_float(__float_as_uint(x.im.lo) ^ m);
+        return r;
+    }
     // Smith's complex division in double-float arithmetic
     __device__ __forceinline__ static V div(V a, V b) {
         V r;
