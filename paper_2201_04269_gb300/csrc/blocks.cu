@@ -378,22 +378,88 @@ __global__ void __launch_bounds__(kTreeThreads) block_tree_kernel(BlockTreeDev t
     }
     const int np = t.A - 1;
     kacc re = {0.0, 0.0}, im = {0.0, 0.0};
+    // units are added in groups of four in plain double, each group's sum compensated
+    cd grp = cd_make(0.0, 0.0);
+    int in_grp = 0;
     for (int64_t u = t.chunk_unit[chunk] + threadIdx.x; u < t.chunk_unit[chunk + 1]; u += blockDim.x) {
         cd pre = cd_make(1.0, 0.0);
         for (int k = 0; k < np; ++k) pre = cmul(pre, Fs[__ldg(t.unit_pre + u * np + k)]);
         cd s = cd_make(0.0, 0.0);
         const int32_t l1 = __ldg(t.unit_leaf + u + 1);
         for (int32_t l = __ldg(t.unit_leaf + u); l < l1; ++l) {
-            const float2 w = __ldg(t.leaf_w + l);
-            cfma(s, cd_make((double)w.x, (double)w.y), Fs[__ldg(t.leaf_f + l)]);
+            const double2 w = __ldg(t.leaf_wd + l);
+            cfma(s, cd_make(w.x, w.y), Fs[__ldg(t.leaf_f + l)]);
         }
-        const cd r = cmul(pre, s);
-        kacc_add(re, r.re);
-        kacc_add(im, r.im);
+        cfma(grp, pre, s);
+        if (++in_grp == 4) {
+            kacc_add(re, grp.re);
+            kacc_add(im, grp.im);
+            grp = cd_make(0.0, 0.0);
+            in_grp = 0;
+        }
     }
+    kacc_add(re, grp.re);
+    kacc_add(im, grp.im);
     kacc ore, oim;
     block_sum(cd_make(re.hi + re.lo, im.hi + im.lo), ore, oim, red);
     if (threadIdx.x == 0) part[slice * t.n_chunks + chunk] = make_d4(ore.hi, ore.lo, oim.hi, oim.lo);
+}
+
+// The same walk in double-float arithmetic: the slice's projected blocks are scaled by an
+// exact power of two 2^-e (e from the largest |re|, |im| among them) into (hi, lo) float
+// pairs in shared memory; a term of A factors then carries 2^(A e), restored in double
+// on the block's partial sum.
+__global__ void __launch_bounds__(kTreeThreads) block_tree_df_kernel(BlockTreeDev t, const cd* __restrict__ F,
+                                                                      int64_t n_slices, d4* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4 * (kTreeThreads / 32)];
+    __shared__ unsigned redu[64];
+    const int64_t chunk = blockIdx.x / n_slices, slice = blockIdx.x % n_slices;
+    const cd* Fg = F + slice * t.n_f;
+    cdf* fs = reinterpret_cast<cdf*>(smem_raw);
+    unsigned m = 0u, m2 = 0u;
+    for (int i = threadIdx.x; i < t.n_f; i += blockDim.x) {
+        const cd v = Fg[i];
+        m = max(m, max(abs_hiword(v.re), abs_hiword(v.im)));
+    }
+    block_max_u2(m, m2, redu);
+    const int e = exponent_of(m);
+    const double sc = pow2d(-max(min(e, 1000), -1000));
+    for (int i = threadIdx.x; i < t.n_f; i += blockDim.x) {
+        const cd v = Fg[i];
+        cdf z;
+        z.re = df_from_double(v.re * sc);
+        z.im = df_from_double(v.im * sc);
+        fs[i] = z;
+    }
+    __syncthreads();
+    const int np = t.A - 1;
+    MIXED::A tot;
+    MIXED::acc_zero(tot);
+    for (int64_t u = t.chunk_unit[chunk] + threadIdx.x; u < t.chunk_unit[chunk + 1]; u += blockDim.x) {
+        cdf pre = MIXED::one();
+        for (int k = 0; k < np; ++k) pre = MIXED::mul(pre, fs[__ldg(t.unit_pre + u * np + k)]);
+        MIXED::A a;
+        MIXED::acc_zero(a);
+        const int32_t l1 = __ldg(t.unit_leaf + u + 1);
+        for (int32_t l = __ldg(t.unit_leaf + u); l < l1; ++l) {
+            const float2 w = __ldg(t.leaf_w + l);
+            const cdf f = fs[__ldg(t.leaf_f + l)];
+            // (w.x + i w.y) f with float weights (exact products by error-free transformation)
+            dacc_fma_f(a.r0, w.x, f.re);
+            dacc_fma_f(a.r1, -w.y, f.im);
+            dacc_fma_f(a.i0, w.x, f.im);
+            dacc_fma_f(a.i1, w.y, f.re);
+        }
+        MIXED::add(tot, MIXED::mul(pre, MIXED::get(a)));
+    }
+    const cd v = MIXED::to_cd(MIXED::get(tot));
+    kacc ore, oim;
+    block_sum(v, ore, oim, red);
+    if (threadIdx.x == 0) {
+        const double back = pow2d(max(min(t.A * e, 1000), -1000));
+        part[slice * t.n_chunks + chunk] = make_d4(ore.hi * back, ore.lo * back, oim.hi * back, oim.lo * back);
+    }
 }
 
 }  // namespace
@@ -469,12 +535,17 @@ cudaError_t launch_blocks_projected(const BlockDev& b, int prec, const double* U
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_tree(const BlockTreeDev& t, const cd* F, int64_t n_slices, d4* part, cudaStream_t s,
-                              int64_t* launches) {
+cudaError_t launch_block_tree(const BlockTreeDev& t, int prec, const cd* F, int64_t n_slices, d4* part,
+                              cudaStream_t s, int64_t* launches) {
     if (n_slices <= 0 || t.n_chunks <= 0) return cudaSuccess;
     const size_t smem = (size_t)t.n_f * 16;
     const int64_t grid = (int64_t)t.n_chunks * n_slices;
-    if (smem <= kSmemBudget) {
+    if (prec == 1 && smem <= kSmemBudget) {
+        cudaError_t e = cudaFuncSetAttribute(block_tree_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        block_tree_df_kernel<<<(unsigned)grid, kTreeThreads, smem, s>>>(t, F, n_slices, part);
+    } else if (smem <= kSmemBudget) {
         cudaError_t e = cudaFuncSetAttribute(block_tree_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;

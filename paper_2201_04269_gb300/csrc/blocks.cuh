@@ -33,7 +33,8 @@ struct BlockTreeDev {
     const uint16_t* unit_pre;      // [n_units][A - 1]
     const int32_t* unit_leaf;      // [n_units + 1]
     const uint16_t* leaf_f;        // [leaves]
-    const float2* leaf_w;          // [leaves] integer-valued weights (exact in float)
+    const float2* leaf_w;          // [leaves] integer-valued weights (exact in float): double-float tree
+    const double2* leaf_wd;        // [leaves] the same in double: FP64 tree
     int n_chunks;
     const int64_t* chunk_unit;     // [n_chunks + 1]
 };
@@ -53,8 +54,9 @@ int64_t block_project_scratch(int n_f, int n_types, int64_t n_slices, int64_t V3
 cudaError_t launch_blocks_projected(const BlockDev& b, int prec, const double* U, const double* D, int64_t n_slices,
                                     int64_t V3, int L, const int* p, cd* part, cd* F, int sms, cudaStream_t s,
                                     int64_t* launches);
-// Factor tree over projected blocks: part [n_slices][t.n_chunks] compensated partial sums.
-cudaError_t launch_block_tree(const BlockTreeDev& t, const cd* F, int64_t n_slices, d4* part, cudaStream_t s,
-                              int64_t* launches);
+// Factor tree over projected blocks: part [n_slices][t.n_chunks] compensated partial sums;
+// prec 0 in complex double, 1 in double-float (the slice's blocks scaled by a power of two).
+cudaError_t launch_block_tree(const BlockTreeDev& t, int prec, const cd* F, int64_t n_slices, d4* part,
+                              cudaStream_t s, int64_t* launches);
 
 }  // namespace mbc

@@ -187,13 +187,17 @@ mbc_status mbc_block_plan_create(mbc_ctx* c, int op, int prec, mbc_block_plan** 
         auto place = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
         const size_t o_e = place(entry.size() * 4), o_pre = place(h.unit_pre.size() * 2),
                      o_ul = place(h.unit_leaf.size() * 4), o_lf = place(h.leaf_f.size() * 2),
-                     o_lw = place(lw.size() * 8), o_cu = place(chunk_unit.size() * 8);
+                     o_lw = place(lw.size() * 8), o_lwd = place(h.w.size() * 16), o_cu = place(chunk_unit.size() * 8);
         std::vector<unsigned char> blob(std::max<size_t>(off, 256));
         std::memcpy(blob.data() + o_e, entry.data(), entry.size() * 4);
         if (!h.unit_pre.empty()) std::memcpy(blob.data() + o_pre, h.unit_pre.data(), h.unit_pre.size() * 2);
         std::memcpy(blob.data() + o_ul, h.unit_leaf.data(), h.unit_leaf.size() * 4);
         std::memcpy(blob.data() + o_lf, h.leaf_f.data(), h.leaf_f.size() * 2);
         std::memcpy(blob.data() + o_lw, lw.data(), lw.size() * 8);
+        for (size_t i = 0; i < h.w.size(); ++i) {
+            const double wd[2] = {h.w[i].real(), h.w[i].imag()};
+            std::memcpy(blob.data() + o_lwd + 16 * i, wd, 16);
+        }
         std::memcpy(blob.data() + o_cu, chunk_unit.data(), chunk_unit.size() * 8);
         e = cudaMalloc(&P->dev, blob.size());
         if (e != cudaSuccess) { delete P; return fail(c, MBC_OOM, std::string("cudaMalloc of block plan: ") + cudaGetErrorString(e)); }
@@ -210,6 +214,7 @@ mbc_status mbc_block_plan_create(mbc_ctx* c, int op, int prec, mbc_block_plan** 
         P->td.unit_leaf = reinterpret_cast<const int32_t*>(base + o_ul);
         P->td.leaf_f = reinterpret_cast<const uint16_t*>(base + o_lf);
         P->td.leaf_w = reinterpret_cast<const float2*>(base + o_lw);
+        P->td.leaf_wd = reinterpret_cast<const double2*>(base + o_lwd);
         P->td.n_chunks = (int)n_chunks;
         P->td.chunk_unit = reinterpret_cast<const int64_t*>(base + o_cu);
     }
@@ -283,7 +288,7 @@ mbc_status mbc_block_correlator(mbc_block_plan* P, const void* U, const void* D,
     if (st != MBC_OK) return st;
     st = ensure(c, c->blk_tree, sizeof(d4) * (size_t)(n_slices * P->td.n_chunks), s);
     if (st != MBC_OK) return st;
-    e = launch_block_tree(P->td, (const cd*)c->blk_F.p, n_slices, (d4*)c->blk_tree.p, s, &c->launches);
+    e = launch_block_tree(P->td, P->hp.prec, (const cd*)c->blk_F.p, n_slices, (d4*)c->blk_tree.p, s, &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "block tree launch");
     Geometry g{n_sets, T, (int64_t)P->td.n_chunks};
     Partials pt{(d4*)c->blk_tree.p, 1};
