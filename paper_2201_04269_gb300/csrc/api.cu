@@ -516,6 +516,7 @@ mbc_status mbc_operator_terms(int op, int* n_u, int* n_d, int* n_free, int64_t* 
 }
 
 mbc_status mbc_plan_create(mbc_ctx* ctx, const mbc_problem* pr, int algo, int prec, mbc_plan** out) {
+    Range range_("mbc_plan_create");
     if (!ctx) return MBC_INVALID_ARG;
     if (!pr || !out) return fail(ctx, MBC_INVALID_ARG, "null problem or output pointer");
     if (algo < 0 || algo > 2 || prec < 0 || prec > 1) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
@@ -560,6 +561,7 @@ mbc_status mbc_plan_create(mbc_ctx* ctx, const mbc_problem* pr, int algo, int pr
 
 mbc_status mbc_plan_from_terms(mbc_ctx* ctx, int n_u, int n_d, int64_t n_terms, const int8_t* sink, const int8_t* source,
                                const double* W, const double* scale, int algo, int prec, mbc_plan** out) {
+    Range range_("mbc_plan_from_terms");
     if (!ctx) return MBC_INVALID_ARG;
     if (!out || n_terms < 0 || (n_terms && (!sink || !source || !W))) return fail(ctx, MBC_INVALID_ARG, "bad term arrays");
     if (algo < 0 || algo > 2 || prec < 0 || prec > 1) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
@@ -649,6 +651,7 @@ mbc_status mbc_plan_save(const mbc_plan* P, const char* path) {
 }
 
 mbc_status mbc_plan_load(mbc_ctx* ctx, const char* path, mbc_plan** out) {
+    Range range_("mbc_plan_load");
     if (!ctx) return MBC_INVALID_ARG;
     if (!path || !out) return fail(ctx, MBC_INVALID_ARG, "null path or output");
     mbc_plan* P = new (std::nothrow) mbc_plan();
@@ -662,6 +665,7 @@ mbc_status mbc_plan_load(mbc_ctx* ctx, const char* path, mbc_plan** out) {
 
 mbc_status mbc_correlator(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int64_t V3, void* C, void* site_out,
                           mbc_stream stream) {
+    Range range_("mbc_correlator");
     if (!P) return MBC_INVALID_ARG;
     mbc_ctx* c = P->ctx;
     if (n_sets < 0 || T < 0 || V3 < 0) return fail(c, MBC_INVALID_ARG, "negative size");
@@ -675,6 +679,7 @@ mbc_status mbc_correlator(mbc_plan* P, const void* U, const void* D, int n_sets,
 
 mbc_status mbc_correlator_momentum(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int L, const int* p,
                                    void* C, void* site_out, mbc_stream stream) {
+    Range range_("mbc_correlator_momentum");
     if (!P) return MBC_INVALID_ARG;
     mbc_ctx* c = P->ctx;
     if (n_sets < 0 || T < 0 || L < 0) return fail(c, MBC_INVALID_ARG, "negative size");
@@ -693,6 +698,7 @@ mbc_status mbc_correlator_momentum(mbc_plan* P, const void* U, const void* D, in
 
 mbc_status mbc_correlator_host(mbc_plan* P, const void* U_host, const void* D_host, int n_sets, int T, int64_t V3,
                                void* C_host, mbc_stream stream) {
+    Range range_("mbc_correlator_host");
     if (!P) return MBC_INVALID_ARG;
     mbc_ctx* c = P->ctx;
     if (n_sets < 0 || T < 0 || V3 < 0) return fail(c, MBC_INVALID_ARG, "negative size");
@@ -748,6 +754,7 @@ mbc_status check_items(mbc_ctx* c, const mbc_work* items, int n_items) {
 }  // namespace
 
 mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
+    Range range_("mbc_batch_reserve");
     if (!c) return MBC_INVALID_ARG;
     mbc_status st = check_items(c, items, n_items);
     if (st != MBC_OK) return st;
@@ -807,6 +814,7 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
 }
 
 mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream stream) {
+    Range range_("mbc_batch");
     if (!c) return MBC_INVALID_ARG;
     mbc_status st = check_items(c, items, n_items);
     if (st != MBC_OK) return st;
@@ -870,6 +878,7 @@ mbc_status mbc_get_schedule(const mbc_plan* P, mbc_schedule* s) {
 }
 
 mbc_status mbc_autotune(mbc_plan* P, const void* U, const void* D, int64_t n_sites, mbc_stream stream, mbc_schedule* best) {
+    Range range_("mbc_autotune");
     if (!P) return MBC_INVALID_ARG;
     mbc_ctx* c = P->ctx;
     if (!U || !D || n_sites <= 0) return fail(c, MBC_INVALID_ARG, "autotune needs fields and a positive site count");

@@ -90,6 +90,7 @@ extern "C" {
 
 mbc_status mbc_hadron_blocks(mbc_ctx* c, int type, const void* U, const void* D, int64_t n_sites, void* f,
                              mbc_stream stream) {
+    Range range_("mbc_hadron_blocks");
     mbc_status st = check_fields(c, U, D, n_sites);
     if (st != MBC_OK) return st;
     if (type < 0 || type >= kBlockTypes) return fail(c, MBC_INVALID_ARG, "unknown block type");
@@ -109,6 +110,7 @@ mbc_status mbc_hadron_blocks(mbc_ctx* c, int type, const void* U, const void* D,
 
 mbc_status mbc_hadron_blocks_projected(mbc_ctx* c, int type, const void* U, const void* D, int n_sets, int T, int L,
                                        const int* p, void* F, mbc_stream stream) {
+    Range range_("mbc_hadron_blocks_projected");
     if (!c) return MBC_INVALID_ARG;
     mbc_status st = check_lattice(c, n_sets, T, L);
     if (st != MBC_OK) return st;
@@ -133,6 +135,7 @@ mbc_status mbc_hadron_blocks_projected(mbc_ctx* c, int type, const void* U, cons
 }
 
 mbc_status mbc_block_plan_create(mbc_ctx* c, int op, int prec, mbc_block_plan** out) {
+    Range range_("mbc_block_plan_create");
     if (!c || !out) return MBC_INVALID_ARG;
     *out = nullptr;
     if (op < 0 || op > MBC_OP_HE3_II_S) return fail(c, MBC_INVALID_ARG, "unknown operator");
@@ -266,6 +269,7 @@ mbc_status mbc_block_plan_get_terms(const mbc_block_plan* P, int32_t* ids, doubl
 
 mbc_status mbc_block_correlator(mbc_block_plan* P, const void* U, const void* D, int n_sets, int T, int L,
                                 const int* p, void* C, mbc_stream stream) {
+    Range range_("mbc_block_correlator");
     if (!P) return MBC_INVALID_ARG;
     mbc_ctx* c = P->ctx;
     mbc_status st = check_lattice(c, n_sets, T, L);

@@ -4,6 +4,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mbc.h"
 #include "device.cuh"
 
@@ -46,5 +48,15 @@ bool capturing(cudaStream_t s);
 mbc_status ensure(mbc_ctx* c, Buf& b, size_t bytes, cudaStream_t s);
 // Free every block plan of the context (blocks_api.cu).
 void destroy_block_plans(mbc_ctx* c);
+
+// NVTX range around an ABI call (a no-op unless a profiler is attached): the planner and
+// every evaluation show up by name on a profiler's timeline, and `ncu --nvtx
+// --nvtx-include "mbc_correlator/"` captures only the kernels of that call.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 }  // namespace mbc

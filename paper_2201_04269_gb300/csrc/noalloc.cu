@@ -23,6 +23,7 @@
 #include "mbc.h"
 
 #include "noalloc.hpp"
+#include "ctx.hpp"
 
 using namespace mbc;
 
@@ -53,6 +54,7 @@ size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
 extern "C" mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, const void* D, int n_sets, int T,
                                              int64_t V3, void* C, mbc_stream stream) {
+    Range range_("mbc_correlator_noalloc");
     if (!plan) return MBC_INVALID_ARG;
     NoallocView v;
     if (!noalloc_view(plan, &v)) return MBC_INVALID_ARG;
