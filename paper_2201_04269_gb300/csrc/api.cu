@@ -313,6 +313,10 @@ std::string signature(const HostPlan& h) {
 
 mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
     HostPlan& h = P->hp;
+    {
+        const std::string bad = validate_plan(h);
+        if (!bad.empty()) { delete P; return fail(ctx, MBC_INVALID_ARG, bad); }
+    }
     if (h.algo == MBC_ALGO_EGRAPH) {
         if (h.explicit_terms) { delete P; return fail(ctx, MBC_UNSUPPORTED, "MBC_ALGO_EGRAPH needs a factored problem (mbc_plan_create)"); }
         if (h.eg.n_j > 64) { delete P; return fail(ctx, MBC_UNSUPPORTED, "e-graph kernels support at most 64 free indices in use"); }
@@ -332,7 +336,12 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
         ctx->err.clear();
         return MBC_OK;
     }
-    mbc_status st = upload(P);
+    mbc_status st;
+    try {
+        st = upload(P);
+    } catch (const std::bad_alloc&) {
+        st = fail(ctx, MBC_OOM, "host allocation while uploading the plan");
+    }
     if (st != MBC_OK) { delete P; return st; }
     if (h.algo == MBC_ALGO_EGRAPH && P->ed.smem_values * 16 > 200 * 1024) {
         cudaFree(P->dev);

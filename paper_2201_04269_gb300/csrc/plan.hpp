@@ -104,6 +104,9 @@ std::string operator_terms(int op, int& n_u, int& n_d, int& n_free, std::vector<
                            std::vector<cplx>& w, std::vector<int64_t>& off, std::vector<cplx>& proj, double& scale);
 double flops_lu(int n);
 
+// structural checks of a plan's device arrays ("" when every index is in range)
+std::string validate_plan(const HostPlan& p);
+
 // serialisation (planner.cpp)
 std::string plan_write(const HostPlan& p, const std::string& path);
 std::string plan_read(HostPlan& p, const std::string& path);

@@ -781,6 +781,106 @@ std::string plan_explicit(HostPlan& p) {
     return "";
 }
 
+// ------------------------------------------------------------------------ validation
+// Structural checks of everything the kernels index with: every table index, offset and
+// count a device array holds lies inside the array it refers to.  Run before a plan is
+// uploaded and after a plan file is read, so that a damaged or hand-made plan is rejected
+// on the host instead of reaching a kernel.
+namespace {
+bool monotone(const std::vector<int32_t>& v, int64_t last) {
+    if (v.empty() || v[0] != 0) return false;
+    for (size_t i = 1; i < v.size(); ++i) if (v[i] < v[i - 1]) return false;
+    return v.back() == last;
+}
+std::string check_minor_plan(const MinorPlan& m, const char* which) {
+    const std::string w(which);
+    if (m.n < 0 || m.n > 6) return w + ": minor size outside 0..6";
+    if (m.n == 0) return "";
+    for (int k = 1; k <= m.n; ++k) {
+        const size_t n = m.level_rows[k].size();
+        if (n == 0 || n > 65535) return w + ": level table size out of range";
+        if (m.child[k].size() != n * k || m.row[k].size() != n * k) return w + ": level table arrays inconsistent";
+        const size_t parent = k == 1 ? 1 : m.level_rows[k - 1].size();
+        for (size_t i = 0; i < n * k; ++i)
+            if (m.child[k][i] >= parent || m.row[k][i] >= 12) return w + ": level table entry out of range";
+    }
+    for (auto& nd : m.nodes)
+        if (nd.level < 1 || nd.level > m.n || nd.col >= 12 || (nd.sign != 1 && nd.sign != -1) || nd.leaf < -1 ||
+            nd.leaf >= (int32_t)m.cols.size())
+            return w + ": column-tree node out of range";
+    return "";
+}
+}  // namespace
+
+std::string validate_plan(const HostPlan& p) {
+    if (p.n_u < 0 || p.n_u > 6 || p.n_d < 0 || p.n_d > 6 || p.n_u + p.n_d == 0) return "plan: n_u, n_d out of range";
+    if (p.algo < 0 || p.algo > 2 || p.prec < 0 || p.prec > 1) return "plan: algorithm or precision out of range";
+    const int nq = p.n_u + p.n_d;
+    for (int8_t v : p.snk_idx) if (v < 0 || v > 11) return "plan: sink index outside 0..11";
+    for (int8_t v : p.src_idx) if (v < 0 || v > 11) return "plan: source index outside 0..11";
+    for (int8_t v : p.ex_snk) if (v < 0 || v > 11) return "plan: sink index outside 0..11";
+    for (int8_t v : p.ex_src) if (v < 0 || v > 11) return "plan: source index outside 0..11";
+    if (p.ex_snk.size() != p.ex_w.size() * nq || p.ex_src.size() != p.ex_w.size() * nq) return "plan: explicit terms inconsistent";
+    if (!p.explicit_terms) {
+        if ((int)p.snk_off.size() != p.n_free + 1 || (int)p.src_off.size() != p.n_free + 1) return "plan: offsets size";
+        for (int j = 0; j < p.n_free; ++j)
+            if (p.snk_off[j] > p.snk_off[j + 1] || p.src_off[j] > p.src_off[j + 1]) return "plan: offsets decrease";
+        if (p.snk_off[0] != 0 || p.src_off[0] != 0 || (size_t)p.snk_off.back() * nq != p.snk_idx.size() ||
+            (size_t)p.src_off.back() * nq != p.src_idx.size() || (size_t)p.snk_off.back() != p.snk_w.size() ||
+            (size_t)p.src_off.back() != p.src_w.size())
+            return "plan: term arrays inconsistent with offsets";
+        if (p.proj.size() != (size_t)p.n_free * p.n_free) return "plan: projector size";
+    }
+    // direct sweep blocks: sink and source ranges inside the term lists
+    const DirectPlan& d = p.direct;
+    const size_t nb = d.blk_s0.size();
+    if (d.blk_s1.size() != nb || d.blk_r0.size() != nb || d.blk_r1.size() != nb || d.blk_p.size() != nb)
+        return "plan: direct blocks inconsistent";
+    for (size_t i = 0; i < nb; ++i)
+        if (d.blk_s0[i] < 0 || d.blk_s0[i] > d.blk_s1[i] || (size_t)d.blk_s1[i] > p.snk_w.size() || d.blk_r0[i] < 0 ||
+            d.blk_r0[i] > d.blk_r1[i] || (size_t)d.blk_r1[i] > p.src_w.size())
+            return "plan: direct block range out of range";
+    // factor tree: two levels, factor ids inside the minor tables, chunks inside the arrays
+    const TreePlan& t = p.tree;
+    if (t.children.size() != t.factors.size()) return "plan: tree arrays inconsistent";
+    const int64_t n_um = (int64_t)t.minor_rows[0].size(), n_dm = (int64_t)t.minor_rows[1].size();
+    if (t.minor_cols[0].size() != (size_t)n_um || t.minor_cols[1].size() != (size_t)n_dm) return "plan: tree minors inconsistent";
+    int64_t leaves = 0;
+    for (size_t i = 1; i < t.factors.size(); ++i) {
+        const int64_t f = t.factors[i];
+        if (t.children[i] < 0 || f < 0 || f >= n_um + n_dm) return "plan: tree factor out of range";
+        if (t.children[i] == 0) ++leaves;
+    }
+    if (leaves != (int64_t)t.coefficients.size()) return "plan: tree leaves and coefficients differ";
+    if (t.chunk_leaf.size() != t.chunk_node.size() || t.chunk_count.size() != t.chunk_node.size())
+        return "plan: tree chunks inconsistent";
+    for (size_t c = 0; c < t.chunk_node.size(); ++c)
+        if (t.chunk_node[c] < 1 || t.chunk_node[c] > (int64_t)t.factors.size() || t.chunk_leaf[c] < 0 ||
+            t.chunk_leaf[c] > (int64_t)t.coefficients.size() || t.chunk_count[c] < 0)
+            return "plan: tree chunk out of range";
+    // e-graph plan
+    const EgraphPlan& e = p.eg;
+    if (p.algo == 2 && !p.terms.empty()) {
+        std::string err = check_minor_plan(e.A, "e-graph A");
+        if (err.empty()) err = check_minor_plan(e.B, "e-graph B");
+        if (!err.empty()) return err;
+        if (e.A.n == 0 || e.n_j < 1 || e.n_j > 64) return "plan: e-graph shape out of range";
+        const int64_t nrb = e.B.n ? (int64_t)e.B.level_rows[e.B.n].size() : 1;
+        const int64_t ncb = e.B.n ? (int64_t)e.B.cols.size() : 1;
+        const int64_t nra = (int64_t)e.A.level_rows[e.A.n].size();
+        if ((int64_t)e.g_off.size() != nrb * e.n_j + 1 || !monotone(e.g_off, (int64_t)e.g_a.size()) ||
+            e.g_w.size() != e.g_a.size())
+            return "plan: e-graph G entries inconsistent";
+        for (int32_t a : e.g_a) if (a < 0 || a >= nra) return "plan: e-graph G entry out of range";
+        if ((int64_t)e.pair_off.size() != (int64_t)e.A.cols.size() + 1 || !monotone(e.pair_off, (int64_t)e.pair_b.size()) ||
+            e.pair_first.size() != e.pair_b.size() || e.pair_coef.size() != e.pair_b.size() * (size_t)e.n_j)
+            return "plan: e-graph pairs inconsistent";
+        for (int32_t b : e.pair_b) if (b < 0 || b >= ncb) return "plan: e-graph pair column out of range";
+        for (uint8_t f : e.pair_first) if (f > 1) return "plan: e-graph first-update flag out of range";
+    }
+    return "";
+}
+
 // ------------------------------------------------------------------------ serialisation
 namespace {
 const char kMagic[8] = {'M', 'B', 'C', 'P', 'L', 'A', 'N', '2'};
@@ -850,7 +950,9 @@ std::string plan_read(HostPlan& p, const std::string& path) {
     plan_io(r, p);
     bool ok = r.ok;
     fclose(f);
-    return ok ? "" : "truncated plan file: " + path;
+    if (!ok) return "truncated plan file: " + path;
+    const std::string bad = validate_plan(p);
+    return bad.empty() ? "" : "damaged plan file (" + bad + "): " + path;
 }
 
 }  // namespace mbc

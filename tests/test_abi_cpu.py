@@ -186,6 +186,32 @@ def test_plan_file_round_trip(abi, hctx, tmp_path):
     abi.mbc_plan_destroy(plan2)
 
 
+def test_damaged_plan_files_are_rejected_on_the_host(abi, hctx, tmp_path):
+    """A plan file whose index arrays were damaged must fail to load (every index a kernel
+    uses is checked on the host), or load as a plan that passes the same checks."""
+    plan, _ = plan_of(abi, hctx, "proton", "egraph", "fp64")
+    p = str(tmp_path / "p.mbcplan")
+    abi.mbc_plan_save(plan, p, hctx)
+    abi.mbc_plan_destroy(plan)
+    raw = open(p, "rb").read()
+    rng = np.random.default_rng(5)
+    detected = 0
+    for k in range(60):
+        buf = bytearray(raw)
+        pos = int(rng.integers(8, len(buf)))
+        buf[pos] ^= 0xFF
+        q = str(tmp_path / f"bad{k}.mbcplan")
+        open(q, "wb").write(bytes(buf))
+        try:
+            ok = abi.mbc_plan_load(hctx, q)
+            abi.mbc_plan_get_info(ok)
+            abi.mbc_plan_destroy(ok)
+        except abi.MbcError as e:
+            assert e.status in (1, 2, 3, 7)
+            detected += "damaged plan file" in abi.mbc_last_error(hctx)
+    assert detected > 0
+
+
 @pytest.mark.parametrize("name", ["dinucleon_I", "he3_I", "he3_II_s"])
 def test_minor_egraph_size_and_flops(abi, hctx, name):
     """The extracted Laplace plan costs less than one LU per minor, and the saturated

@@ -320,6 +320,38 @@ def test_random_complex_factored(ctx, algo, prec):
     plan.destroy()
 
 
+@pytest.mark.parametrize("n_u,n_d", [(6, 6), (6, 0), (0, 5), (1, 6)])
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_largest_and_single_flavour_minors(ctx, n_u, n_d, algo, prec):
+    """The largest minors the ABI takes (6 x 6 per flavour) and one-flavour problems
+    (an empty minor has determinant 1), on random factored weights."""
+    rng = np.random.default_rng(100 * n_u + n_d)
+    from paper_2201_04269_gb300 import abi, Plan
+
+    def side(n):
+        idx = np.zeros((n, n_u + n_d), np.int8)
+        for t in range(n):
+            idx[t, :n_u] = rng.choice(12, n_u, replace=False)
+            idx[t, n_u:] = rng.choice(12, n_d, replace=False)
+        return idx, rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    si, sw = side(20)
+    ri, rw = side(16)
+    soff, roff = np.array([0, 9, 20]), np.array([0, 7, 16])
+    P = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    plan = Plan(ctx, abi.mbc_plan_create(ctx.handle, n_u, n_d, si, sw, soff, ri, rw, roff, P, 1.0, algo, prec))
+    U, D = mi.workload_fields("proton_4x8", L=2, T=2)
+    C, S = run(plan, U[None], D[None])
+    snk = [(si[soff[j]:soff[j + 1]], sw[soff[j]:soff[j + 1]]) for j in range(2)]
+    src = [(ri[roff[j]:roff[j + 1]], rw[roff[j]:roff[j + 1]]) for j in range(2)]
+    n = n_u + n_d
+    # the oracle applies the Wick sign of n slots; the plan's scale is 1
+    ref = (-1) ** (n * (n - 1) // 2) * onat.direct(n_u, n_d, snk, src, P, U.reshape(-1, 12, 12),
+                                                    D.reshape(-1, 12, 12))
+    check(S[0].ravel(), ref, prec)
+    plan.destroy()
+
+
 def _batched_items(ctx, prec, n_sets=2):
     """Items of the batched workload, scaled down: every operator on two lattice sizes,
     n_sets propagator sets each (seeds and sets as in the workload recipe)."""
