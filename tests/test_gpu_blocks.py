@@ -208,3 +208,32 @@ def test_block_correlator_deterministic(ctx):
         outs.append(C.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
     plan.destroy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_translation_full_size(ctx, prec):
+    """3He_II-s on the full 24^3 lattice (two slices): translating the sink fields by a
+    lattice vector a leaves the zero-momentum block correlator unchanged and multiplies
+    the one at momentum p by e^{-i 2 pi A p.a / L} (every one of the A baryons picks up
+    the phase of its own projection) -- a property of the exact result at any size."""
+    L = 24
+    U, D = fields("he3_24x48", t_list=[5, 40])
+    x = np.arange(L ** 3)
+    xyz = np.stack([x % L, (x // L) % L, x // (L * L)], axis=1)
+    a = np.array([3, 0, 7])
+    moved = ((xyz + a) % L) @ np.array([1, L, L * L])
+    Us, Ds = np.empty_like(U), np.empty_like(D)
+    Us[:, moved], Ds[:, moved] = U, D
+    plan = ctx.block_plan("he3_II_s", prec)
+    p = (1, 2, 0)
+    out = {}
+    for key, (uu, dd, mom) in {"0": (U, D, None), "0s": (Us, Ds, None), "p": (U, D, p), "ps": (Us, Ds, p)}.items():
+        C = torch.zeros(1, 2, dtype=torch.complex128, device="cuda")
+        plan.correlator(dev(uu[None]), dev(dd[None]), C, L, mom)
+        torch.cuda.synchronize()
+        out[key] = C.cpu().numpy()[0]
+    tol = 1e-10 if prec == "fp64" else 1e-9
+    assert np.max(np.abs(out["0s"] - out["0"]) / np.abs(out["0"])) <= tol
+    phase = np.exp(-2j * np.pi * 3 * np.dot(p, a) / L)
+    assert np.max(np.abs(out["ps"] - out["p"] * phase) / np.abs(out["p"])) <= tol
+    plan.destroy()

@@ -66,3 +66,33 @@ def test_zero_momentum_is_the_plain_sum(ctx):
     torch.cuda.synchronize()
     assert np.array_equal(S0.cpu().numpy(), S2.cpu().numpy())
     plan.destroy()
+
+
+def test_translation_phase_at_benchmark_lattice(ctx):
+    """3He_II-s, 24^3 lattice, two slices, mixed e-graph plan: translating the sink fields
+    by a multiplies C(p) by e^{-i 2 pi p.a / L} and leaves C(0) unchanged (exact property,
+    any size)."""
+    L = 24
+    U, D = mi.workload_fields("he3_24x48", t_list=[3, 33])
+    x = np.arange(L ** 3)
+    xyz = np.stack([x % L, (x // L) % L, x // (L * L)], axis=1)
+    a = np.array([5, 11, 2])
+    moved = ((xyz + a) % L) @ np.array([1, L, L * L])
+    Us, Ds = np.empty_like(U), np.empty_like(D)
+    Us[:, moved], Ds[:, moved] = U, D
+    plan = ctx.plan_operator("he3_II_s", "egraph", "mixed")
+    p = (2, 0, 1)
+    res = []
+    for uu, dd in ((U, D), (Us, Ds)):
+        C0 = torch.zeros(1, 2, dtype=torch.complex128, device="cuda")
+        Cp = torch.zeros(1, 2, dtype=torch.complex128, device="cuda")
+        plan.correlator_momentum(dev(uu[None]), dev(dd[None]), C0, L, None)
+        plan.correlator_momentum(dev(uu[None]), dev(dd[None]), Cp, L, p)
+        torch.cuda.synchronize()
+        res.append((C0.cpu().numpy()[0], Cp.cpu().numpy()[0]))
+    (c0, cp), (c0s, cps) = res
+    # the site sum of C(0) is reordered by the translation: equal within the summation's rounding
+    assert np.max(np.abs(c0s - c0) / np.abs(c0)) <= 1e-9
+    phase = np.exp(-2j * np.pi * np.dot(p, a) / L)
+    assert np.max(np.abs(cps - cp * phase) / np.abs(cp)) <= 1e-9
+    plan.destroy()
