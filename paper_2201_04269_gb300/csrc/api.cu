@@ -226,6 +226,12 @@ mbc_status upload(mbc_plan* P) {
             prec_.push_back(r);
         }
     size_t o_prec = b.add(prec_);
+    std::vector<uint8_t> jmask(e.pair_off.empty() ? 0 : e.pair_off.size() - 1, 0);
+    for (size_t l = 0; l + 1 < e.pair_off.size(); ++l)
+        for (int32_t q = e.pair_off[l]; q < e.pair_off[l + 1]; ++q)
+            for (int j = 0; j < e.n_j && j < 8; ++j)
+                if (e.pair_coef[(size_t)q * e.n_j + j] != 0.0) jmask[l] |= (uint8_t)(1u << j);
+    size_t o_jm = b.add(jmask);
 
     void* dev = nullptr;
     cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
@@ -286,6 +292,7 @@ mbc_status upload(mbc_plan* P) {
     ed.pair_coef = at<Val16>(dev, o_pc);
     ed.sell = at<int2>(dev, o_sell); ed.sell_off = at<int32_t>(dev, o_soff); ed.sell_w = at<int32_t>(dev, o_sellw);
     ed.pair_rec = at<int4>(dev, o_prec);
+    ed.leaf_jmask = at<uint8_t>(dev, o_jm);
     // levels 0..n-1 plus two buffers for the leaf level; G only for the general leaf path
     ed.stack_a = ed.A.off[ed.A.n] + 2 * ed.A.size[ed.A.n];
     ed.stack_b = ed.B.off[ed.B.n] + 2 * ed.B.size[ed.B.n];

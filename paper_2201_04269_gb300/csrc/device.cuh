@@ -103,6 +103,8 @@ struct EgraphDev {
     // pairs of the fused leaf path (n_j <= 2, weights exact in float): (B column |
     // first update << 31, float bits of coef_0, of coef_1, 0)
     const int4* pair_rec;
+    // per A leaf: bit j set when some pair of the leaf has coef_j != 0 (fused leaf path)
+    const uint8_t* leaf_jmask;
 };
 
 // One item of a batched launch: a plan's device view, its fields, where its per-site

@@ -77,6 +77,8 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
     const int n_rb = d.n_rows_b;
     const int p0 = __ldg(d.pair_off + leaf), p1 = __ldg(d.pair_off + leaf + 1);
     const int lane = threadIdx.x & 31;
+    // free indices whose G the leaf's pairs use (the others are skipped)
+    const int jmask = __ldg(d.leaf_jmask + leaf);
     for (int b = threadIdx.x; b < n_rb; b += blockDim.x) {
         V g[NJ];
         const int sl = b >> 5;      // slice of 32 row sets (blockDim is a multiple of 32)
@@ -84,6 +86,10 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
         for (int j = 0; j < NJ; ++j) {
             typename P::A acc;
             P::acc_zero(acc);
+            if (!((jmask >> j) & 1)) {
+                g[j] = P::zero();
+                continue;
+            }
             if (P::kind == 1) {
                 // double-float: issue-bound, coalesced sliced-ELL records (padding is cheap)
                 const int2* ent = d.sell + __ldg(d.sell_off + sl * NJ + j) + lane;
@@ -115,11 +121,13 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
                 typename P::A h0, h1;
                 P::acc_set(h0, v0);
                 P::acc_set(h1, v1);
-                P::fma_s(h0, (S)__int_as_float(r0.y), g[0]);
-                P::fma_s(h1, (S)__int_as_float(r1.y), g[0]);
+                // zero coefficients are skipped: the branches are uniform (every thread of
+                // the block handles the same pair)
+                if (r0.y) P::fma_s(h0, (S)__int_as_float(r0.y), g[0]);
+                if (r1.y) P::fma_s(h1, (S)__int_as_float(r1.y), g[0]);
                 if (NJ > 1) {
-                    P::fma_s(h0, (S)__int_as_float(r0.z), g[NJ - 1]);
-                    P::fma_s(h1, (S)__int_as_float(r1.z), g[NJ - 1]);
+                    if (r0.z) P::fma_s(h0, (S)__int_as_float(r0.z), g[NJ - 1]);
+                    if (r1.z) P::fma_s(h1, (S)__int_as_float(r1.z), g[NJ - 1]);
                 }
                 *k0 = P::get_s(h0);
                 *k1 = P::get_s(h1);
@@ -130,8 +138,8 @@ __device__ __forceinline__ void leaf_fused(const EgraphDev& d, int leaf, const t
                 typename P::A h;
                 if (rec.x < 0) P::acc_zero(h);
                 else P::acc_set(h, *kp);
-                P::fma_s(h, (S)__int_as_float(rec.y), g[0]);
-                if (NJ > 1) P::fma_s(h, (S)__int_as_float(rec.z), g[NJ - 1]);
+                if (rec.y) P::fma_s(h, (S)__int_as_float(rec.y), g[0]);
+                if (NJ > 1 && rec.z) P::fma_s(h, (S)__int_as_float(rec.z), g[NJ - 1]);
                 *kp = P::get_s(h);
             }
         } else {

@@ -604,7 +604,31 @@ static void build_egraph(HostPlan& p, const std::vector<int>& used_j, const std:
     bool real = true;
     for (auto& x : e.g_w) real = real && x.imag() == 0.0;
     for (auto& x : e.pair_coef) real = real && x.imag() == 0.0;
-    e.flops_per_site = 8.0 * egraph_cost(p, fa, e.A, e.B, used_j, used_jp, real ? 0.5 : 1.0);
+    // algorithmic flops of the built plan: the Laplace tables of both trees, the G entries of
+    // the free indices each A leaf's pairs use, one multiply-add per nonzero pair
+    // coefficient and B row set, and the final dot products (real weights: half a complex
+    // multiply-add each)
+    {
+        const double wf = real ? 0.5 : 1.0;
+        const int64_t nrb = e.B.n ? (int64_t)e.B.level_rows[e.B.n].size() : 1;
+        const int64_t ncb = e.B.n ? (int64_t)e.B.cols.size() : 1;
+        std::vector<int64_t> nnz_j(n_j, 0);
+        for (int64_t b = 0; b < nrb; ++b)
+            for (int jj = 0; jj < n_j; ++jj) nnz_j[jj] += e.g_off[b * n_j + jj + 1] - e.g_off[b * n_j + jj];
+        double cf = e.A.dp_cfma + e.B.dp_cfma + (double)ncb * (double)nrb;
+        for (size_t l = 0; l + 1 < e.pair_off.size(); ++l) {
+            uint32_t used = 0;
+            for (int32_t q = e.pair_off[l]; q < e.pair_off[l + 1]; ++q)
+                for (int jj = 0; jj < n_j; ++jj)
+                    if (e.pair_coef[(size_t)q * n_j + jj] != 0.0) {
+                        used |= 1u << (jj & 31);
+                        cf += wf * (double)nrb;
+                    }
+            for (int jj = 0; jj < n_j; ++jj)
+                if (n_j > 32 || ((used >> jj) & 1)) cf += wf * (double)nnz_j[jj];
+        }
+        e.flops_per_site = 8.0 * cf;
+    }
     p.eg = std::move(e);
     p.flops_egraph = p.eg.flops_per_site;
 }
