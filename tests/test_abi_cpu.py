@@ -186,6 +186,58 @@ def test_plan_file_round_trip(abi, hctx, tmp_path):
     abi.mbc_plan_destroy(plan2)
 
 
+@pytest.mark.parametrize("n_u,n_d,seed", [(1, 1, 0), (2, 1, 1), (3, 2, 2), (4, 4, 3), (6, 0, 4), (2, 5, 5), (6, 6, 6)])
+def test_planner_on_random_factored_problems(abi, hctx, n_u, n_d, seed):
+    """Random factored problems (repeated indices, Gaussian-integer weights, a projector with
+    zeros): the planner's linearised tree expands to exactly the oracle's canonical terms
+    (row and column sets, merged weights, Wick sign), and every algorithm's plan passes the
+    structural checks."""
+    rng = np.random.default_rng(seed)
+    n_free, per_j = 2, 12
+    terms = []
+    for j in range(n_free):
+        d = {}
+        for _ in range(per_j):
+            a_u = tuple(int(v) for v in rng.integers(0, 12, n_u))
+            a_d = tuple(int(v) for v in rng.integers(0, 12, n_d))
+            w = complex(int(rng.integers(-3, 4)), int(rng.integers(-2, 3)))
+            if w != 0:
+                d[(a_u, a_d)] = d.get((a_u, a_d), 0) + w
+        terms.append({k: v for k, v in d.items() if v != 0})
+    proj = np.array([[1.0, 0.5j], [0.0, -2.0]], dtype=np.complex128)
+    op = oops.Operator("random", n_u, n_d, terms, proj, 1.0)
+    idx, w, off = [], [], [0]
+    for j in range(n_free):
+        a, b = op.arrays(j)
+        idx.append(a.reshape(-1, n_u + n_d))
+        w.append(b)
+        off.append(off[-1] + len(b))
+    idx, w, off = np.concatenate(idx), np.concatenate(w), np.array(off)
+    scale = wick_sign(n_u + n_d)
+    for algo in ("direct", "tree", "egraph"):
+        plan = abi.mbc_plan_create(hctx, n_u, n_d, idx, w, off, idx, w, off, proj, scale, algo, "fp64")
+        abi.mbc_plan_destroy(plan)
+    plan = abi.mbc_plan_create(hctx, n_u, n_d, idx, w, off, idx, w, off, proj, scale, "tree", "fp64")
+    f, ch, co = abi.mbc_plan_get_tree(plan)
+    n_umin = abi.mbc_plan_get_info(plan)["minors_u"]
+    got = {}
+    k, leaf = 1, 0
+    while k < len(f):
+        mu = abi.mbc_plan_get_minor(plan, 0, int(f[k]), n_u)
+        n = ch[k]
+        k += 1
+        for _ in range(n):
+            md = abi.mbc_plan_get_minor(plan, 1, int(f[k]) - n_umin, n_d)
+            got[(mu, md)] = co[leaf] * scale
+            k += 1
+            leaf += 1
+    ref = {((ru, cu), (rd, cd)): wv for ru, rd, cu, cd, wv in ocan.canonical_terms(op)}
+    assert got.keys() == ref.keys()
+    for key in ref:
+        assert abs(got[key] - ref[key]) <= 1e-12 * max(1.0, abs(ref[key]))
+    abi.mbc_plan_destroy(plan)
+
+
 def test_damaged_plan_files_are_rejected_on_the_host(abi, hctx, tmp_path):
     """A plan file whose index arrays were damaged must fail to load (every index a kernel
     uses is checked on the host), or load as a plan that passes the same checks."""
