@@ -25,10 +25,13 @@
  *    row = sink index, column = source index; it is owned by the caller.
  *  - Calls never throw; they return an mbc_status.  Failed calls leave outputs
  *    unchanged and record a message readable through mbc_last_error(ctx).
- *  - Device work is enqueued on the caller's stream and is asynchronous; a plan is
- *    immutable after creation and may be used from several streams at once as long as
- *    each call has its own output buffers.  No call synchronises the device except
- *    where stated.
+ *  - Device work is enqueued on the caller's stream and is asynchronous.  No call
+ *    synchronises the device except where stated.
+ *  - A plan is immutable after creation.  The evaluation calls of one context share
+ *    its scratch pool (per-site partial sums, per-block K slots, the work counter, the
+ *    block buffers), so their device work must not overlap: issue them on one stream,
+ *    or give each stream its own context (and plans).  A context is used by one host
+ *    thread at a time.
  */
 #ifndef MBC_H
 #define MBC_H
