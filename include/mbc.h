@@ -329,6 +329,10 @@ mbc_status mbc_block_plan_get_info(const mbc_block_plan* plan, mbc_block_plan_in
 /* Merged terms: ids [merged_terms][A] (type * MBC_BLOCK_ENTRIES + eta, ascending within
  * a term), w [merged_terms][2] complex double (normalisation included); host memory. */
 mbc_status mbc_block_plan_get_terms(const mbc_block_plan* plan, int32_t* ids, double* w);
+/* Multiplicity of every merged term (how many expanded terms it merges; Sec. 3 and the
+ * multiplicity histograms of its Fig. 2): int32 [merged_terms], host memory, in the order
+ * of mbc_block_plan_get_terms. */
+mbc_status mbc_block_plan_get_multiplicities(const mbc_block_plan* plan, int32_t* multiplicity);
 mbc_status mbc_block_correlator(mbc_block_plan* plan, const void* U, const void* D, int n_sets, int T, int L,
                                 const int* p, void* C, mbc_stream stream);
 

@@ -114,6 +114,7 @@ SIGNATURES = [
     ("mbc_block_plan_destroy", None, [c_vp]),
     ("mbc_block_plan_get_info", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_block_plan_info)]),
     ("mbc_block_plan_get_terms", ctypes.c_int, [c_vp, c_i32p, c_dp]),
+    ("mbc_block_plan_get_multiplicities", ctypes.c_int, [c_vp, c_i32p]),
     ("mbc_block_correlator", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_i32p,
                                             c_vp, c_vp]),
 ]
@@ -386,6 +387,15 @@ def mbc_block_plan_get_terms(plan):
     if K:
         check(load().mbc_block_plan_get_terms(plan, ids.ctypes.data_as(c_i32p), w.view(np.float64).ctypes.data_as(c_dp)))
     return ids, w
+
+
+def mbc_block_plan_get_multiplicities(plan):
+    """Multiplicity of every merged block term: int32 [K]."""
+    K = mbc_block_plan_get_info(plan)["merged_terms"]
+    m = np.zeros(K, np.int32)
+    if K:
+        check(load().mbc_block_plan_get_multiplicities(plan, m.ctypes.data_as(c_i32p)))
+    return m
 
 
 def mbc_block_correlator(plan, U, D, n_sets, T, L, C, p=None, stream=None, ctx=None):

@@ -48,6 +48,7 @@ struct BlockHostPlan {
     double scale = 1.0;                    // sink norm x source norm
     std::vector<int32_t> ids;              // merged terms [K][A], global ids (type * kEta + eta), ascending
     std::vector<cplx> w;                   // [K] merged weights (integer valued, scale not applied)
+    std::vector<int32_t> multiplicity;     // [K] expanded terms merged into each (Sec. 3)
     std::vector<int32_t> factor;           // distinct global ids, ascending: compact index = position
     std::vector<int> types;                // block types used, ascending
     // device walk of the factor tree: a unit is a level A-2 vertex (A >= 2; its path

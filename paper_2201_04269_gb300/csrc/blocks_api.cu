@@ -267,6 +267,12 @@ mbc_status mbc_block_plan_get_terms(const mbc_block_plan* P, int32_t* ids, doubl
     return MBC_OK;
 }
 
+mbc_status mbc_block_plan_get_multiplicities(const mbc_block_plan* P, int32_t* multiplicity) {
+    if (!P || !multiplicity) return MBC_INVALID_ARG;
+    std::copy(P->hp.multiplicity.begin(), P->hp.multiplicity.end(), multiplicity);
+    return MBC_OK;
+}
+
 mbc_status mbc_block_correlator(mbc_block_plan* P, const void* U, const void* D, int n_sets, int T, int L,
                                 const int* p, void* C, mbc_stream stream) {
     Range range_("mbc_block_correlator");

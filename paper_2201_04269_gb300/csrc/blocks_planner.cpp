@@ -167,6 +167,7 @@ std::string plan_blocks(BlockHostPlan& bp) {
     std::sort(terms.begin(), terms.end(), [](const KeyW& a, const KeyW& b) { return a.key < b.key; });
     bp.ids.clear();
     bp.w.clear();
+    bp.multiplicity.clear();
     for (size_t i = 0; i < terms.size();) {
         size_t k = i;
         double re = 0, im = 0;
@@ -177,6 +178,7 @@ std::string plan_blocks(BlockHostPlan& bp) {
             for (int a = A - 1; a >= 0; --a) { id[a] = (int32_t)(key & 0xffff); key >>= 16; }
             bp.ids.insert(bp.ids.end(), id, id + A);
             bp.w.push_back(cplx(re, im));
+            bp.multiplicity.push_back((int32_t)(k - i));
         }
         i = k;
     }

@@ -36,6 +36,7 @@ def test_block_plan_matches_oracle(abi, hctx, name):
     ids, w = abi.mbc_block_plan_get_terms(plan)
     assert np.array_equal(ids, ref.ids)
     np.testing.assert_allclose(w, ref.W, rtol=1e-15, atol=0)
+    assert np.array_equal(abi.mbc_block_plan_get_multiplicities(plan), ref.multiplicity)
     # factors and factor-tree levels from the merged terms
     assert info["factors"] == len(np.unique(ref.ids)) if ref.n_terms else info["factors"] == 0
     for a in range(ref.A):
