@@ -223,11 +223,15 @@ def run_blocks(args, rank, world, local):
     D = torch.from_numpy(D_h).cuda()
     C = torch.zeros(n_sets, n_t, dtype=torch.complex128, device="cuda")
     ctx = Context(local)
-    plan = ctx.block_plan(args.op, args.prec)
+    local_form = args.algo == "blocks_local"
+    plan = ctx.block_plan(args.op, "fp64" if local_form else args.prec)
     info = plan.info
 
     def step():
-        plan.correlator(U, D, C, Lb, stream=stream)
+        if local_form:
+            plan.correlator_local(U, D, C, stream=stream)
+        else:
+            plan.correlator(U, D, C, Lb, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -251,11 +255,14 @@ def run_blocks(args, rank, world, local):
         ms = float(t.item())
     clocks = clk.summary()
     sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
-    flops = info["block_flops_per_site"] * n_sites + info["tree_flops_per_slice"] * n_sets * n_t
+    prec = "fp64" if local_form else args.prec
+    # the local form walks the whole block tree at every site
+    flops = (info["block_flops_per_site"] * n_sites +
+             info["tree_flops_per_slice"] * (n_sites if local_form else n_sets * n_t))
     achieved = flops / (ms * 1e-3) / 1e12
-    peak = fp64_peak_tflops(sm_max) if args.prec == "fp64" else fp32_peak_tflops(sm_max)
+    peak = fp64_peak_tflops(sm_max) if prec == "fp64" else fp32_peak_tflops(sm_max)
     headline_shape = (args.op == OPERATOR and (Lb, Tb) == (L, T) and args.slices <= 0 and args.sets == 1)
-    tps = recorded_traffic_per_site(BLOCK_TRAFFIC_FILE, BLOCK_SOURCES) if headline_shape else None
+    tps = recorded_traffic_per_site(BLOCK_TRAFFIC_FILE, BLOCK_SOURCES) if headline_shape and not local_form else None
     # end to end: pinned host fields copied in, C copied out, inside the timed region
     U_pin = torch.from_numpy(U_h).pin_memory()
     D_pin = torch.from_numpy(D_h).pin_memory()
@@ -269,14 +276,13 @@ def run_blocks(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if rank == 0:
-        line = {"metric": f"sink-site contractions/sec ({args.op} block form, zero-momentum projected blocks, "
-                          f"{Lb}^3x{Tb}, {args.prec})",
+        form = "local sink" if local_form else "zero-momentum projected blocks"
+        line = {"metric": f"sink-site contractions/sec ({args.op} block form, {form}, {Lb}^3x{Tb}, {prec})",
                 "value": world * n_sites / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32x2" if args.prec == "mixed" else "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32x2" if prec == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": f"{args.op} {Lb}^3x{Tb}" + (f" ({n_t} slices)" if n_t != Tb else "") +
-                                       f", {n_sets} source(s) per GPU, block form (every baryon projected to p = 0)"
-                                       f", {args.prec}",
+                                       f", {n_sets} source(s) per GPU, block form ({form}), {prec}",
                            "sites_per_gpu": n_sites,
                            "l2": f"inputs {2 * U_h.nbytes / 1e9:.2f} GB per GPU" +
                                  (", larger than L2" if 2 * U_h.nbytes > 129e6 else ", smaller than L2"),
@@ -284,12 +290,13 @@ def run_blocks(args, rank, world, local):
                                                                "level_nodes")}},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": None if tps is None else tps * n_sites,
-                             "kernel": "block_project_kernel + block_tree_kernel",
+                             "kernel": ("block_local_kernel" if local_form else
+                                        "block_project_kernel + block_tree_kernel"),
                              "kernel_source_hash": kernel_hash(BLOCK_SOURCES),
                              "flops_per_site": info["block_flops_per_site"],
                              "tree_flops_per_slice": info["tree_flops_per_slice"],
                              "peak_basis": (f"FP64: {SM_COUNT} SMs x {FP64_FMA_PER_SM} DFMA/cycle x 2 x {sm_max:.0f} MHz "
-                                            "(derived)" if args.prec == "fp64" else
+                                            "(derived)" if prec == "fp64" else
                                             f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
                                             "(derived)")},
                 "cpu_baseline": None,
@@ -311,8 +318,9 @@ def main():
     ap.add_argument("--fp64-slices", type=int, default=4)
     # other workloads and algorithms (the default is the benchmark's headline configuration)
     ap.add_argument("--op", default=OPERATOR)
-    ap.add_argument("--algo", default="egraph", choices=["egraph", "tree", "direct", "blocks"],
-                    help="blocks = hadron blocks projected to zero momentum and the block factor tree (FP64)")
+    ap.add_argument("--algo", default="egraph", choices=["egraph", "tree", "direct", "blocks", "blocks_local"],
+                    help="blocks = hadron blocks projected to zero momentum and the block factor tree; "
+                         "blocks_local = the block form of the local-sink correlator (FP64)")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--lattice", default=f"{L}x{T}", help="L x T, e.g. 16x32")
     ap.add_argument("--slices", type=int, default=0, help="time slices evaluated (0 = all)")
@@ -341,7 +349,7 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
 
-    if args.algo == "blocks":
+    if args.algo in ("blocks", "blocks_local"):
         run_blocks(args, rank, world, local)
         if world > 1:
             dist.destroy_process_group()

@@ -335,6 +335,15 @@ mbc_status mbc_block_plan_get_terms(const mbc_block_plan* plan, int32_t* ids, do
 mbc_status mbc_block_plan_get_multiplicities(const mbc_block_plan* plan, int32_t* multiplicity);
 mbc_status mbc_block_correlator(mbc_block_plan* plan, const void* U, const void* D, int n_sets, int T, int L,
                                 const int* p, void* C, mbc_stream stream);
+/* The block form of the local-sink correlator: C[s][t] = sum_x C_x with
+ *     C_x = sum_k w_k prod_i f^{h_ik}(x; eta_ik),
+ * every baryon at the same sink site x -- the same quantity as mbc_correlator for the
+ * operator (U, D [n_sets][T][V3][12][12], C [n_sets][T], site_out optional
+ * [n_sets][T][V3], as for mbc_correlator).  One block of threads per site builds the
+ * site's blocks in shared memory and walks the block factor tree over them.  FP64 plans;
+ * MBC_UNSUPPORTED when the plan's block entries do not fit shared memory. */
+mbc_status mbc_block_correlator_local(mbc_block_plan* plan, const void* U, const void* D, int n_sets, int T,
+                                      int64_t V3, void* C, void* site_out, mbc_stream stream);
 
 /* Number of device kernel launches made by this context since it was created (every
  * launch of every mbc call counts once). */

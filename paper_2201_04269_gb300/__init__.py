@@ -129,5 +129,10 @@ class BlockPlan:
         n_sets, T = U.shape[:2]
         abi.mbc_block_correlator(self.handle, U, D, n_sets, T, L, C, p, stream, self.ctx.handle)
 
+    def correlator_local(self, U, D, C, site_out=None, stream=None):
+        """Local sink (the quantity of Plan.correlator): U, D [n_sets, T, V3, 12, 12]; C [n_sets, T]."""
+        n_sets, T, V3 = U.shape[:3]
+        abi.mbc_block_correlator_local(self.handle, U, D, n_sets, T, V3, C, site_out, stream, self.ctx.handle)
+
 
 __all__ = ["abi", "Context", "Plan", "BlockPlan", "MbcError", "ALGO", "PREC", "OPERATOR"]

@@ -115,6 +115,8 @@ SIGNATURES = [
     ("mbc_block_plan_get_info", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_block_plan_info)]),
     ("mbc_block_plan_get_terms", ctypes.c_int, [c_vp, c_i32p, c_dp]),
     ("mbc_block_plan_get_multiplicities", ctypes.c_int, [c_vp, c_i32p]),
+    ("mbc_block_correlator_local", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                                  c_vp, c_vp, c_vp]),
     ("mbc_block_correlator", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_i32p,
                                             c_vp, c_vp]),
 ]
@@ -400,3 +402,9 @@ def mbc_block_plan_get_multiplicities(plan):
 
 def mbc_block_correlator(plan, U, D, n_sets, T, L, C, p=None, stream=None, ctx=None):
     check(load().mbc_block_correlator(plan, dptr(U), dptr(D), n_sets, T, L, _mom(p), dptr(C), sptr(stream)), ctx)
+
+
+def mbc_block_correlator_local(plan, U, D, n_sets, T, V3, C, site_out=None, stream=None, ctx=None):
+    """The block form of the local-sink correlator (same quantity as mbc_correlator)."""
+    check(load().mbc_block_correlator_local(plan, dptr(U), dptr(D), n_sets, T, V3, dptr(C), dptr(site_out),
+                                            sptr(stream)), ctx)

@@ -462,6 +462,60 @@ __global__ void __launch_bounds__(kTreeThreads) block_tree_df_kernel(BlockTreeDe
     }
 }
 
+// The block form of the local-sink correlator (every baryon at the same sink site x):
+//     C_x = sum_k w_k prod_i f^{h_ik}(x; eta_ik),
+// which is the quark-level correlator of the same operator.  One block per site at a
+// time: the site's block entries are built in shared memory (diquark tables, then the
+// entries the plan uses), and the whole block factor tree is walked over them; the
+// site's compensated sum goes to its partial.  Complex double.
+__global__ void __launch_bounds__(kThreads) block_local_kernel(BlockDev b, BlockTreeDev t,
+                                                                const double* __restrict__ U,
+                                                                const double* __restrict__ D, int64_t n_sites,
+                                                                d4* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockTypeDev ty[6];
+    __shared__ double red[4 * (kThreads / 32)];
+    cd* q = reinterpret_cast<cd*>(smem_raw);
+    cd* dq = q + 2 * kQ;
+    cd* fs = dq + b.n_types * kDq;
+    load_types(b, ty);
+    const int np = t.A - 1;
+    for (int64_t site = blockIdx.x; site < n_sites; site += gridDim.x) {
+        __syncthreads();
+        stage_site(U, D, site, q);
+        __syncthreads();
+        diquarks(b.n_types, ty, q, dq);
+        __syncthreads();
+        for (int f = threadIdx.x; f < b.n_f; f += blockDim.x) fs[f] = block_entry(ty, entry_code(b, f), q, dq);
+        __syncthreads();
+        kacc re = {0.0, 0.0}, im = {0.0, 0.0};
+        cd grp = cd_make(0.0, 0.0);
+        int in_grp = 0;
+        for (int64_t u = threadIdx.x; u < t.n_units; u += blockDim.x) {
+            cd pre = cd_make(1.0, 0.0);
+            for (int k = 0; k < np; ++k) pre = cmul(pre, fs[__ldg(t.unit_pre + u * np + k)]);
+            cd s = cd_make(0.0, 0.0);
+            const int32_t l1 = __ldg(t.unit_leaf + u + 1);
+            for (int32_t l = __ldg(t.unit_leaf + u); l < l1; ++l) {
+                const double2 w = __ldg(t.leaf_wd + l);
+                cfma(s, cd_make(w.x, w.y), fs[__ldg(t.leaf_f + l)]);
+            }
+            cfma(grp, pre, s);
+            if (++in_grp == 4) {
+                kacc_add(re, grp.re);
+                kacc_add(im, grp.im);
+                grp = cd_make(0.0, 0.0);
+                in_grp = 0;
+            }
+        }
+        kacc_add(re, grp.re);
+        kacc_add(im, grp.im);
+        kacc ore, oim;
+        block_sum(cd_make(re.hi + re.lo, im.hi + im.lo), ore, oim, red);
+        if (threadIdx.x == 0) part[site] = make_d4(ore.hi, ore.lo, oim.hi, oim.lo);
+    }
+}
+
 }  // namespace
 
 int block_entries_per_cta(int n_types) { return (int)(kSmemBudget / 16) - 2 * kQ - n_types * kDq; }
@@ -553,6 +607,24 @@ cudaError_t launch_block_tree(const BlockTreeDev& t, int prec, const cd* F, int6
     } else {
         block_tree_kernel<false><<<(unsigned)grid, kTreeThreads, 0, s>>>(t, F, n_slices, part);
     }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace mbc
+
+namespace mbc {
+
+cudaError_t launch_block_local(const BlockDev& b, const BlockTreeDev& t, const double* U, const double* D,
+                               int64_t n_sites, d4* part, int sms, cudaStream_t s, int64_t* launches) {
+    if (n_sites <= 0) return cudaSuccess;
+    const size_t smem = block_kernel_smem(b.n_f, b.n_types, true);
+    if (smem > kSmemBudget) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(block_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int per_sm = std::max(1, (int)((227 * 1024) / (smem + 2 * 1024)));
+    const int64_t grid = std::min<int64_t>(n_sites, (int64_t)sms * std::min(per_sm, 2048 / kThreads));
+    block_local_kernel<<<(unsigned)grid, kThreads, smem, s>>>(b, t, U, D, n_sites, part);
     ++*launches;
     return cudaGetLastError();
 }

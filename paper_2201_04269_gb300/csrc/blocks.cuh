@@ -54,6 +54,11 @@ int64_t block_project_scratch(int n_f, int n_types, int64_t n_slices, int64_t V3
 cudaError_t launch_blocks_projected(const BlockDev& b, int prec, const double* U, const double* D, int64_t n_slices,
                                     int64_t V3, int L, const int* p, cd* part, cd* F, int sms, cudaStream_t s,
                                     int64_t* launches);
+// Local-sink block form: part [n_sites] = per-site compensated sums of the block factor
+// tree over the site's own blocks (complex double); cudaErrorInvalidValue when the
+// plan's block entries do not fit shared memory.
+cudaError_t launch_block_local(const BlockDev& b, const BlockTreeDev& t, const double* U, const double* D,
+                               int64_t n_sites, d4* part, int sms, cudaStream_t s, int64_t* launches);
 // Factor tree over projected blocks: part [n_slices][t.n_chunks] compensated partial sums;
 // prec 0 in complex double, 1 in double-float (the slice's blocks scaled by a power of two).
 cudaError_t launch_block_tree(const BlockTreeDev& t, int prec, const cd* F, int64_t n_slices, d4* part,

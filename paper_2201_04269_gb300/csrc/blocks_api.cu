@@ -267,6 +267,46 @@ mbc_status mbc_block_plan_get_terms(const mbc_block_plan* P, int32_t* ids, doubl
     return MBC_OK;
 }
 
+mbc_status mbc_block_correlator_local(mbc_block_plan* P, const void* U, const void* D, int n_sets, int T, int64_t V3,
+                                      void* C, void* site_out, mbc_stream stream) {
+    Range range_("mbc_block_correlator_local");
+    if (!P) return MBC_INVALID_ARG;
+    mbc_ctx* c = P->ctx;
+    if (n_sets < 0 || T < 0 || V3 < 0) return fail(c, MBC_INVALID_ARG, "negative size");
+    const int64_t n_sites = (int64_t)n_sets * T * V3, n_slices = (int64_t)n_sets * T;
+    mbc_status st = check_fields(c, U, D, n_sites);
+    if (st != MBC_OK) return st;
+    if (n_slices > 0 && !C) return fail(c, MBC_INVALID_ARG, "null output");
+    if (n_sites > ((int64_t)1 << 32)) return fail(c, MBC_UNSUPPORTED, "more than 2^32 sites in one call");
+    if (P->hp.prec != MBC_PREC_FP64) return fail(c, MBC_UNSUPPORTED, "the local block form evaluates in MBC_PREC_FP64 plans");
+    if (!P->hp.w.empty() && block_kernel_smem(P->bd.n_f, P->bd.n_types, true) > 200 * 1024)
+        return fail(c, MBC_UNSUPPORTED, "the plan's block entries do not fit shared memory for the local block form");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_slices == 0) { c->err.clear(); return MBC_OK; }
+    if (P->hp.w.empty() || n_sites == 0) {
+        e = cudaMemsetAsync(C, 0, sizeof(double2) * (size_t)n_slices, s);
+        if (e == cudaSuccess && site_out && n_sites) e = cudaMemsetAsync(site_out, 0, sizeof(double2) * (size_t)n_sites, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+        c->err.clear();
+        return MBC_OK;
+    }
+    st = ensure(c, c->partials, sizeof(d4) * (size_t)n_sites, s);
+    if (st == MBC_OK && site_out) st = ensure(c, c->site_tmp, sizeof(d4) * (size_t)n_sites, s);
+    if (st != MBC_OK) return st;
+    e = launch_block_local(P->bd, P->td, (const double*)U, (const double*)D, n_sites, (d4*)c->partials.p, c->sms, s,
+                           &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "local block kernel launch");
+    Geometry g{n_sets, T, V3};
+    Partials pt{(d4*)c->partials.p, 1};
+    e = launch_reduce(pt, g, cd_make(P->hp.scale, 0.0), (double2*)C, (double2*)site_out, (d4*)c->site_tmp.p, s,
+                      &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reduction launch");
+    c->err.clear();
+    return MBC_OK;
+}
+
 mbc_status mbc_block_plan_get_multiplicities(const mbc_block_plan* P, int32_t* multiplicity) {
     if (!P || !multiplicity) return MBC_INVALID_ARG;
     std::copy(P->hp.multiplicity.begin(), P->hp.multiplicity.end(), multiplicity);

@@ -237,3 +237,43 @@ def test_translation_full_size(ctx, prec):
     phase = np.exp(-2j * np.pi * 3 * np.dot(p, a) / L)
     assert np.max(np.abs(out["ps"] - out["p"] * phase) / np.abs(out["p"])) <= tol
     plan.destroy()
+
+
+@pytest.mark.parametrize("name,wl,L,T", [("proton", "proton_4x8", 3, 2), ("dinucleon_I", "dinucleon_16x32", 3, 2),
+                                         ("he3_I", "he3_24x48", 2, 2), ("he3_II_s", "he3_24x48", 2, 1)])
+def test_local_block_form_matches_determinant_oracle(ctx, name, wl, L, T):
+    """The block form of the local-sink correlator (blocks of each site, block factor tree
+    per site) against the quark-level oracle, per site and summed, and against the
+    e-graph plan on the GPU."""
+    U, D = fields(wl, L=L, T=T)
+    cp = ocor.CanonicalPlan(oops.build(name))
+    want_sites = cp.site_values(U.reshape(-1, 12, 12), D.reshape(-1, 12, 12))
+    want = ocor.correlator(cp.site_values, U, D)
+    plan = ctx.block_plan(name)
+    C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    S = torch.zeros(1, T, L ** 3, dtype=torch.complex128, device="cuda")
+    plan.correlator_local(dev(U[None]), dev(D[None]), C, S)
+    qp = ctx.plan_operator(name, "egraph", "fp64")
+    Cq = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+    qp.correlator(dev(U[None]), dev(D[None]), Cq)
+    torch.cuda.synchronize()
+    got, sites = C.cpu().numpy()[0], S.cpu().numpy().ravel()
+    assert np.max(np.abs(sites - want_sites) / np.abs(want_sites)) <= TOL
+    assert np.max(np.abs(got - want) / np.abs(want)) <= TOL
+    assert np.max(np.abs(Cq.cpu().numpy()[0] - got) / np.abs(got)) <= TOL
+    plan.destroy()
+    qp.destroy()
+
+
+def test_local_block_form_vanishing_and_empty(ctx):
+    U, D = fields("dinucleon_16x32", L=2, T=2)
+    plan = ctx.block_plan("dinucleon_II")
+    C = torch.full((1, 2), complex(1.0, 2.0), dtype=torch.complex128, device="cuda")
+    plan.correlator_local(dev(U[None]), dev(D[None]), C)
+    torch.cuda.synchronize()
+    assert np.all(C.cpu().numpy() == 0)
+    plan.destroy()
+    plan = ctx.block_plan("proton")
+    C = torch.zeros(0, 2, dtype=torch.complex128, device="cuda")
+    plan.correlator_local(dev(U[None][:0]), dev(D[None][:0]), C)
+    plan.destroy()
