@@ -297,8 +297,9 @@ mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, const void* D, 
  * with every sink baryon projected to momentum p (p, U, D, C as above; C device complex
  * double [n_sets][T], written): the paper's block setting.  On an L = 1 lattice it
  * equals the local-sink correlator of mbc_correlator.  prec: MBC_PREC_FP64 (complex
- * double throughout) or MBC_PREC_MIXED (the projected blocks in double-float
- * arithmetic with power-of-two site scaling, the factor tree in complex double).
+ * double throughout) or MBC_PREC_MIXED (double-float arithmetic: the projected blocks
+ * with power-of-two site scaling, the factor tree over blocks scaled per slice; the
+ * tile and slice sums in compensated double).
  * ---------------------------------------------------------------------------------- */
 #define MBC_BLOCK_ENTRIES 6912
 typedef enum {
