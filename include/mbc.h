@@ -16,8 +16,10 @@
  * with scale carrying (-1)^{n(n-1)/2} and any normalisation.  Three algorithms:
  * the direct index-set sweep (MBC_ALGO_DIRECT), factor trees (Sec. 4,
  * MBC_ALGO_TREE) and a plan extracted from a tensor e-graph (Sec. 5, MBC_ALGO_EGRAPH);
- * two arithmetics: complex double (MBC_PREC_FP64) and complex FP32 pairs with
- * compensated products and double accumulation (MBC_PREC_MIXED).
+ * three arithmetics: complex double (MBC_PREC_FP64), complex FP32 pairs with
+ * compensated products and double accumulation (MBC_PREC_MIXED, "double-float"), and
+ * complex FP32 with compensated sums and a per-site error guard (MBC_PREC_FP32, e-graph
+ * plans only; see mbc_plan_set_guard).
  *
  * Conventions for every call:
  *  - Spin-colour index i = 3 * spin + colour in 0..11.  A propagator field is a device
@@ -57,7 +59,7 @@ typedef enum {
 } mbc_status;
 
 typedef enum { MBC_ALGO_DIRECT = 0, MBC_ALGO_TREE = 1, MBC_ALGO_EGRAPH = 2 } mbc_algo;
-typedef enum { MBC_PREC_FP64 = 0, MBC_PREC_MIXED = 1 } mbc_prec;
+typedef enum { MBC_PREC_FP64 = 0, MBC_PREC_MIXED = 1, MBC_PREC_FP32 = 2 } mbc_prec;
 
 typedef struct mbc_ctx mbc_ctx;
 typedef struct mbc_plan mbc_plan;
@@ -217,6 +219,32 @@ mbc_status mbc_batch_reserve(mbc_ctx* ctx, const mbc_work* items, int n_items);
 mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_stream stream);
 
 /* ------------------------------------------------------------------------------------
+ * The FP32 arithmetic of e-graph plans (MBC_PREC_FP32).
+ *
+ * The minors (Laplace steps of the extracted column trees, Sec. 5), the G stage and the
+ * pair products run in complex FP32 on each site's propagators scaled by exact powers
+ * of two; every thread sums its parts with TwoSum compensation and the site sum is a
+ * compensated double sum.  FP32 rounding (2^-24 per operation) reaches the site value
+ * amplified by the cancellation of the site sum (the floating-point problem cited in
+ * Sec. 1), so every site also gets an error estimate
+ *     est = sqrt(sum over the site's (A leaf, B row set) parts of |part|^2) / |C_x|
+ * and every site with est > threshold (or a non-finite estimate) is recomputed by the
+ * double-float kernel (the arithmetic of MBC_PREC_MIXED) in a second launch on the same
+ * stream, before the site sum.  Measured on He-3 workloads, the FP32 error of a site is
+ * about 1e-7 x est; the default threshold 3 keeps it below 1e-6.  threshold = +inf
+ * recomputes no site (plain FP32), threshold <= 0 recomputes every site.
+ *
+ * mbc_plan_set_guard / mbc_plan_get_guard: the plan's threshold (host call, takes effect
+ * for evaluations issued afterwards).  mbc_fp32_recomputed: the number of sites that the
+ * last MBC_PREC_FP32 evaluation of this context recomputed (synchronises the device;
+ * 0 if none ran).  Results are bit-reproducible for a given plan, threshold, sizes and
+ * device.
+ * ---------------------------------------------------------------------------------- */
+mbc_status mbc_plan_set_guard(mbc_plan* plan, double threshold);
+mbc_status mbc_plan_get_guard(const mbc_plan* plan, double* threshold);
+mbc_status mbc_fp32_recomputed(mbc_ctx* ctx, int64_t* n_sites);
+
+/* ------------------------------------------------------------------------------------
  * Launch schedule and autotuning.  A schedule is (threads per block, blocks per SM,
  * sites per work unit); mbc_autotune times the candidate schedules of the plan's
  * kernel on the given fields (a few sites per candidate), keeps the fastest in the
@@ -232,19 +260,24 @@ mbc_status mbc_get_schedule(const mbc_plan* plan, mbc_schedule* s);
 /* ------------------------------------------------------------------------------------
  * Evaluation without device allocation.  The paper has no counterpart to this entry
  * point; it serves callers that may not allocate device memory at the moment they
- * evaluate: code running while a stream is captured into a CUDA graph, services whose
- * device memory budget is fixed up front, hosts that forbid allocation after start up.
+ * evaluate: services whose device memory is carved out once at start up and must not
+ * grow (an allocation could fail or take memory promised to another tenant), plug-ins
+ * inside a host application that owns every device allocation, and real-time loops
+ * that cannot afford an allocation's latency and implicit synchronisation.
  *
  * mbc_correlator_noalloc computes exactly what mbc_correlator computes (C only, no
  * per-site output) for an MBC_ALGO_EGRAPH plan, with every temporary (work counter,
  * per-site partial sums, the kernel's K slots) taken from one fixed device array of
  * MBC_NOALLOC_SCRATCH_BYTES bytes built into the library; it calls no cudaMalloc,
- * cudaFree or other allocating routine.  The caller still supplies the fields U, D
- * and the output C (device memory, same layouts as mbc_correlator); the plan must
+ * cudaFree or other allocating routine.  (MBC_PREC_FP32 plans are evaluated here in
+ * the double-float arithmetic of MBC_PREC_MIXED.)  The caller still supplies the fields
+ * U, D and the output C (device memory, same layouts as mbc_correlator); the plan must
  * have been created beforehand (plan creation allocates).
  *  - Every GPU that loads this part of the library holds the array until the process
- *    exits.  The first call on a device looks up the array's device address; make that
- *    first call before any stream capture that is to include later calls.
+ *    exits.  The first call on a device looks up the array's device address (with that
+ *    device current) and keeps it for the life of the process; a device reset
+ *    (cudaDeviceReset) invalidates it, and the entry point is then not usable again in
+ *    that process.
  *  - All calls share the array and it keeps the last call's contents (the work counter
  *    is cleared on the stream at each call; nothing else needs to start at zero).
  *    Calls whose device work overlaps (different streams, or different host threads on
@@ -252,6 +285,7 @@ mbc_status mbc_get_schedule(const mbc_plan* plan, mbc_schedule* s);
  *  - A call needing more than the array holds (32 bytes per sink site plus one K slot
  *    of the plan, |cols_B| x |rows_B| x 16 bytes, plus 256) returns MBC_UNSUPPORTED
  *    and a message giving the sizes; fewer K slots than blocks reduce the grid instead.
+ *    Plans with an empty canonical term set (C = 0) are not size-limited.
  * ---------------------------------------------------------------------------------- */
 #define MBC_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, const void* D, int n_sets, int T, int64_t V3,

@@ -33,6 +33,11 @@ class Context:
     def launches(self):
         return abi.mbc_launch_count(self.handle)
 
+    @property
+    def fp32_recomputed(self):
+        """Sites the last MBC_PREC_FP32 evaluation recomputed in double-float (synchronises)."""
+        return abi.mbc_fp32_recomputed(self.handle)
+
     def plan(self, problem: dict, algo="egraph", prec="fp64"):
         """Plan a factored problem (dict with n_u, n_d, idx, w, offsets, proj, scale and
         optionally src_idx/src_w/src_offsets; the source defaults to the sink)."""
@@ -96,6 +101,15 @@ class Plan:
     def correlator_host(self, U, D, C, stream=None):
         n_sets, T, V3 = U.shape[:3]
         abi.mbc_correlator_host(self.handle, U, D, n_sets, T, V3, C, stream, self.ctx.handle)
+
+    def set_guard(self, threshold):
+        """Error-estimate threshold of an MBC_PREC_FP32 plan (sites above it are recomputed
+        in double-float arithmetic)."""
+        abi.mbc_plan_set_guard(self.handle, threshold, self.ctx.handle)
+
+    @property
+    def guard(self):
+        return abi.mbc_plan_get_guard(self.handle)
 
     def autotune(self, U, D, n_sites, stream=None):
         return abi.mbc_autotune(self.handle, U, D, n_sites, stream, self.ctx.handle)

@@ -25,7 +25,7 @@ c_vp = ctypes.c_void_p
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "NUMERIC", 7: "IO"}
 ALGO = {"direct": 0, "tree": 1, "egraph": 2}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "fp32": 2}
 OPERATOR = {"proton": 0, "neutron": 1, "dinucleon_I": 2, "dinucleon_II": 3, "he3_I": 4, "he3_II": 5, "he3_II_s": 6}
 BLOCK_TYPE = {"P": 0, "N": 1, "P+": 2, "P-": 3, "N+": 4, "N-": 5}
 BLOCK_ENTRIES = 6912
@@ -106,6 +106,9 @@ SIGNATURES = [
     ("mbc_set_schedule", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_schedule)]),
     ("mbc_get_schedule", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_schedule)]),
     ("mbc_launch_count", ctypes.c_int64, [c_vp]),
+    ("mbc_plan_set_guard", ctypes.c_int, [c_vp, ctypes.c_double]),
+    ("mbc_plan_get_guard", ctypes.c_int, [c_vp, c_dp]),
+    ("mbc_fp32_recomputed", ctypes.c_int, [c_vp, c_i64p]),
     ("mbc_correlator_noalloc", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, c_vp, c_vp]),
     ("mbc_hadron_blocks", ctypes.c_int, [c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp]),
     ("mbc_hadron_blocks_projected", ctypes.c_int, [c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int, ctypes.c_int,
@@ -344,6 +347,22 @@ def mbc_get_schedule(plan):
     s = mbc_schedule()
     check(load().mbc_get_schedule(plan, ctypes.byref(s)))
     return dict(threads=s.threads, blocks_per_sm=s.blocks_per_sm, sites_per_unit=s.sites_per_unit)
+
+
+def mbc_plan_set_guard(plan, threshold, ctx=None):
+    check(load().mbc_plan_set_guard(plan, float(threshold)), ctx)
+
+
+def mbc_plan_get_guard(plan):
+    v = ctypes.c_double()
+    check(load().mbc_plan_get_guard(plan, ctypes.byref(v)))
+    return v.value
+
+
+def mbc_fp32_recomputed(ctx):
+    n = ctypes.c_int64()
+    check(load().mbc_fp32_recomputed(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
 
 
 # ------------------------------------------------------------------- hadron blocks

@@ -1,6 +1,7 @@
 // api.cu - the C ABI of libmbc (see include/mbc.h): contexts, plans, device upload,
 // evaluation, batching, autotuning and plan files.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -11,10 +12,16 @@
 #include "mbc.h"
 #include "device.cuh"
 #include "plan.hpp"
+#include "walk.hpp"
 #include "noalloc.hpp"
 #include "ctx.hpp"
 
 using namespace mbc;
+
+namespace {
+// Default error-estimate threshold of MBC_PREC_FP32 plans (see include/mbc.h).
+constexpr double kDefaultGuard = 3.0;
+}
 
 struct mbc_plan {
     mbc_ctx* ctx = nullptr;
@@ -24,7 +31,10 @@ struct mbc_plan {
     DirectDev dd{};
     TreeDev td{};
     EgraphDev ed{};
+    Eg32Dev e32{};                // FP32 e-graph view (MBC_PREC_FP32 plans)
     mbc_schedule sched{256, 2, 1};
+    mbc_schedule sched_df{384, 1, 1};   // the double-float recompute of flagged sites (MBC_PREC_FP32)
+    double guard = kDefaultGuard;
     std::string signature;
 };
 
@@ -116,6 +126,177 @@ void minor_dev_offsets(const MinorPlan& m, int upto, int* size, int* off) {
         off[k] = acc;
         if (k <= upto) acc += size[k];
     }
+}
+
+// ---------------------------------------------------------------- FP32 e-graph arrays
+struct F32Offsets {
+    bool used = false;
+    size_t steps[2], step_off[2], leaves[2], pk, sell_off, sell_w, sell, sellc, pair_off, pair_cb, pair_cf, jmask;
+};
+
+// Walker count and leaf batch size that fit the kernel's shared memory: as many walkers
+// (up to 8, i.e. 1024 threads) and then as large a batch (up to 6) as fit.
+int f32_smem(int W, int LB, int pk_words, int stack_vals, int leaf_size) {
+    return 2 * kBlk * 8 + pk_words * 4 + W * (stack_vals + LB * leaf_size) * 8;
+}
+
+std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
+    const EgraphPlan& e = h.eg;
+    if (e.n_j < 1 || e.n_j > 4) return "MBC_PREC_FP32 supports at most 4 free indices in use";
+    const MinorPlan* mp[2] = {&e.A, &e.B};
+    WalkDev* wd[2] = {&v.A, &v.B};
+    int stack[2] = {0, 0};
+    int pk_words = 0;
+    for (int f = 0; f < 2; ++f) {
+        const MinorPlan& m = *mp[f];
+        WalkDev& x = *wd[f];
+        x = WalkDev();
+        x.n = m.n;
+        x.size[0] = 1;
+        for (int k = 1; k < 7; ++k) x.size[k] = k <= m.n ? (int)m.level_rows[k].size() : 0;
+        int acc = 0;
+        for (int k = 0; k < 7; ++k) {
+            x.off[k] = acc;
+            if (k < m.n) acc += x.size[k];
+        }
+        stack[f] = std::max(1, acc);
+        for (int k = 1; k <= m.n; ++k) {
+            x.pk_off[k] = pk_words;
+            pk_words += x.size[k] * k;
+        }
+    }
+    pk_words = (pk_words + 3) / 4 * 4;
+    const int nA = e.A.n;
+    const int leaf_size = v.A.size[nA];
+    const int stack_vals = std::max(stack[0], stack[1]);
+    int W = 0, LB = 0;
+    for (int w : {8, 4, 2, 1}) {
+        for (int lb = 6; lb >= 1 && !W; --lb)
+            if (f32_smem(w, lb, pk_words, stack_vals, leaf_size) <= 220 * 1024) { W = w; LB = lb; }
+        if (W) break;
+    }
+    if (!W) return "MBC_PREC_FP32: the plan's tables do not fit shared memory";
+    const int nrb = e.B.n ? (int)e.B.level_rows[e.B.n].size() : 1;
+    const int ncb = e.B.n ? (int)e.B.cols.size() : 1;
+    const int nj = e.n_j;
+    // walker programs, leaves balanced by cost
+    std::vector<int64_t> nnz_j(nj, 0);
+    for (int rb = 0; rb < nrb; ++rb)
+        for (int j = 0; j < nj; ++j) nnz_j[j] += e.g_off[rb * nj + j + 1] - e.g_off[rb * nj + j];
+    std::vector<double> costA(e.A.cols.size(), 0.0), costB(e.B.n ? e.B.cols.size() : 1, 1.0);
+    for (size_t l = 0; l < costA.size(); ++l) {
+        const int np = e.pair_off[l + 1] - e.pair_off[l];
+        double c = 4.0 * nA * leaf_size + (double)nrb * (16.0 + 10.0 * np);
+        for (int j = 0; j < nj; ++j) {
+            bool used = false;
+            for (int q = e.pair_off[l]; q < e.pair_off[l + 1]; ++q) used = used || e.pair_coef[(size_t)q * nj + j] != 0.0;
+            if (used) c += 2.0 * nnz_j[j];
+        }
+        costA[l] = c;
+    }
+    Walks wk[2];
+    std::string err = build_walks(e.A, W, LB, costA, wk[0]);
+    if (err.empty()) err = build_walks(e.B, W, 255, costB, wk[1]);
+    if (!err.empty()) return err;
+    for (int f = 0; f < 2; ++f) {
+        o.steps[f] = b.add(wk[f].steps);
+        o.step_off[f] = b.add(wk[f].step_off);
+        o.leaves[f] = b.add(wk[f].leaves);
+    }
+    // packed Laplace words (transposed per level), A levels then B levels
+    std::vector<uint32_t> pk(pk_words, 0u);
+    for (int f = 0; f < 2; ++f) {
+        const MinorPlan& m = *mp[f];
+        for (int k = 1; k <= m.n; ++k) {
+            const size_t n = m.level_rows[k].size();
+            for (size_t q = 0; q < n; ++q)
+                for (int i = 0; i < k; ++i)
+                    pk[wd[f]->pk_off[k] + i * n + q] =
+                        (uint32_t)m.child[k][q * k + i] | ((uint32_t)m.row[k][q * k + i] << 16);
+        }
+    }
+    o.pk = b.add(pk);
+    // G entries in sliced-ELL form (FP32 weights)
+    bool real = true;
+    for (auto& x : e.g_w) real = real && x.imag() == 0.0;
+    for (auto& x : e.pair_coef) real = real && x.imag() == 0.0;
+    std::vector<int32_t> soff, sw;
+    std::vector<int2> sr;
+    std::vector<int4> sc;
+    const int n_slices = (nrb + 31) / 32;
+    size_t rec = 0;
+    for (int sl = 0; sl < n_slices; ++sl)
+        for (int j = 0; j < nj; ++j) {
+            int width = 0;
+            for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
+                const int it = (sl * 32 + l) * nj + j;
+                width = std::max(width, e.g_off[it + 1] - e.g_off[it]);
+            }
+            soff.push_back((int32_t)rec);
+            sw.push_back(width);
+            if (real) sr.resize(rec + (size_t)width * 32, int2{0, 0});
+            else sc.resize(rec + (size_t)width * 32, int4{0, 0, 0, 0});
+            for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
+                const int it = (sl * 32 + l) * nj + j;
+                for (int k = 0; k < e.g_off[it + 1] - e.g_off[it]; ++k) {
+                    const int a = e.g_a[e.g_off[it] + k];
+                    const float wr = (float)e.g_w[e.g_off[it] + k].real(), wi = (float)e.g_w[e.g_off[it] + k].imag();
+                    int br, bi;
+                    std::memcpy(&br, &wr, 4);
+                    std::memcpy(&bi, &wi, 4);
+                    if (real) sr[rec + (size_t)k * 32 + l] = int2{a, br};
+                    else sc[rec + (size_t)k * 32 + l] = int4{a, br, bi, 0};
+                }
+            }
+            rec += (size_t)width * 32;
+        }
+    o.sell_off = b.add(soff);
+    o.sell_w = b.add(sw);
+    o.sell = b.add(sr);
+    o.sellc = b.add(sc);
+    std::vector<float2> cf(e.pair_coef.size());
+    for (size_t q = 0; q < cf.size(); ++q) cf[q] = make_float2((float)e.pair_coef[q].real(), (float)e.pair_coef[q].imag());
+    o.pair_off = b.add(e.pair_off);
+    o.pair_cb = b.add(e.pair_b);
+    o.pair_cf = b.add(cf);
+    std::vector<uint8_t> jm(e.A.cols.size(), 0);
+    for (size_t l = 0; l < jm.size(); ++l)
+        for (int q = e.pair_off[l]; q < e.pair_off[l + 1]; ++q)
+            for (int j = 0; j < nj; ++j)
+                if (e.pair_coef[(size_t)q * nj + j] != 0.0) jm[l] |= (uint8_t)(1u << j);
+    o.jmask = b.add(jm);
+    v.flav_a = e.flav_a;
+    v.n_j = nj;
+    v.real_w = real ? 1 : 0;
+    v.walkers = W;
+    v.lb = LB;
+    v.n_rows_b = nrb;
+    v.n_cols_b = ncb;
+    v.stack_vals = stack_vals;
+    v.leafbuf_vals = LB * leaf_size;
+    v.pk_words = pk_words;
+    v.smem_bytes = f32_smem(W, LB, pk_words, stack_vals, leaf_size);
+    o.used = true;
+    return "";
+}
+
+void bind_f32(Eg32Dev& v, void* dev, const F32Offsets& o, float guard) {
+    WalkDev* wd[2] = {&v.A, &v.B};
+    for (int f = 0; f < 2; ++f) {
+        wd[f]->steps = at<WalkStep>(dev, o.steps[f]);
+        wd[f]->step_off = at<int32_t>(dev, o.step_off[f]);
+        wd[f]->leaves = at<WalkLeaf>(dev, o.leaves[f]);
+    }
+    v.pk = at<uint32_t>(dev, o.pk);
+    v.sell_off = at<int32_t>(dev, o.sell_off);
+    v.sell_w = at<int32_t>(dev, o.sell_w);
+    v.sell = at<int2>(dev, o.sell);
+    v.sellc = at<int4>(dev, o.sellc);
+    v.pair_off = at<int32_t>(dev, o.pair_off);
+    v.pair_cb = at<int32_t>(dev, o.pair_cb);
+    v.pair_cf = at<float2>(dev, o.pair_cf);
+    v.leaf_jmask = at<uint8_t>(dev, o.jmask);
+    v.guard = guard;
 }
 
 mbc_status upload(mbc_plan* P) {
@@ -232,6 +413,11 @@ mbc_status upload(mbc_plan* P) {
             for (int j = 0; j < e.n_j && j < 8; ++j)
                 if (e.pair_coef[(size_t)q * e.n_j + j] != 0.0) jmask[l] |= (uint8_t)(1u << j);
     size_t o_jm = b.add(jmask);
+    F32Offsets f32;
+    if (h.prec == MBC_PREC_FP32 && h.algo == MBC_ALGO_EGRAPH && !h.terms.empty()) {
+        std::string err = add_f32(h, P->e32, b, f32);
+        if (!err.empty()) return fail(P->ctx, MBC_UNSUPPORTED, err);
+    }
 
     void* dev = nullptr;
     cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
@@ -307,6 +493,7 @@ mbc_status upload(mbc_plan* P) {
     ed.stage_pk = (base + pk16) * 16 <= 200 * 1024 &&
                   (h.prec == MBC_PREC_FP64 || resident(base + pk16) >= resident(base));
     ed.smem_values = base + (ed.stage_pk ? pk16 : 0);
+    if (f32.used) bind_f32(P->e32, dev, f32, (float)P->guard);
     return MBC_OK;
 }
 
@@ -366,6 +553,8 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
         P->sched.threads = (rows_w > 256 && rows_w <= 384) ? rows_w : 384;
         const int by_smem = (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024));
         P->sched.blocks_per_sm = std::max(1, std::min(by_smem, 2048 / P->sched.threads));
+        P->sched_df = P->sched;
+        if (h.prec == MBC_PREC_FP32) P->sched = mbc_schedule{128 * std::max(1, P->e32.walkers), 1, 1};
     }
     ctx->plans.push_back(P);
     *out = P;
@@ -423,6 +612,23 @@ mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int
         if (st == MBC_OK) st = ensure(c, c->exps, sizeof(int) * 2 * (size_t)wave, s);
         if (st != MBC_OK) return st;
         e = launch_tree(P->td, h.prec, u, d, g, c->scratch.p, wave, (int*)c->exps.p, parts, P->sched.threads, s, &c->launches);
+    } else if (h.prec == MBC_PREC_FP32) {
+        // FP32 pass (one block per SM, a B table per block), then the double-float
+        // kernel over the sites whose error estimate exceeded the guard
+        const int grid32 = (int)std::min<int64_t>(n_sites, (int64_t)c->sms);
+        const int grid_df = (int)std::min<int64_t>(n_sites, (int64_t)c->sms * P->sched_df.blocks_per_sm);
+        st = ensure(c, c->bslot, sizeof(float2) * (size_t)P->e32.n_cols_b * P->e32.n_rows_b * grid32, s);
+        if (st == MBC_OK) st = ensure(c, c->flags, sizeof(unsigned int) * (size_t)n_sites, s);
+        if (st == MBC_OK) st = ensure(c, c->scratch, egraph_kslot_bytes(P->ed) * (size_t)grid_df, s);
+        if (st != MBC_OK) return st;
+        unsigned int* cnt = (unsigned int*)c->counter.p;
+        e = cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess)
+            e = launch_egraph32(P->e32, u, d, g, parts.part, grid32, c->bslot.p, cnt, cnt + 1,
+                                (unsigned int*)c->flags.p, s, &c->launches);
+        if (e == cudaSuccess)
+            e = launch_egraph_list(P->ed, u, d, parts, P->sched_df.threads, grid_df, cnt + 2, c->scratch.p,
+                                   (const unsigned int*)c->flags.p, cnt + 1, s, &c->launches);
     } else {
         const int grid = (int)std::min<int64_t>(n_sites, (int64_t)c->sms * P->sched.blocks_per_sm);
         st = ensure(c, c->scratch, egraph_kslot_bytes(P->ed) * (size_t)grid, s);
@@ -501,7 +707,8 @@ void mbc_destroy(mbc_ctx* c) {
     for (mbc_plan* p : c->plans) { if (p->dev) cudaFree(p->dev); delete p; }
     destroy_block_plans(c);
     Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
-                   &c->batch_items, &c->batch_parts, &c->batch_k, &c->blk_part, &c->blk_F, &c->blk_tree};
+                   &c->batch_items, &c->batch_parts, &c->batch_k, &c->blk_part, &c->blk_F, &c->blk_tree,
+                   &c->bslot, &c->flags};
     for (Buf* b : bufs) if (b->p) cudaFree(b->p);
     delete c;
 }
@@ -535,7 +742,9 @@ mbc_status mbc_plan_create(mbc_ctx* ctx, const mbc_problem* pr, int algo, int pr
     Range range_("mbc_plan_create");
     if (!ctx) return MBC_INVALID_ARG;
     if (!pr || !out) return fail(ctx, MBC_INVALID_ARG, "null problem or output pointer");
-    if (algo < 0 || algo > 2 || prec < 0 || prec > 1) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
+    if (algo < 0 || algo > 2 || prec < 0 || prec > 2) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
+    if (prec == MBC_PREC_FP32 && algo != MBC_ALGO_EGRAPH)
+        return fail(ctx, MBC_UNSUPPORTED, "MBC_PREC_FP32 is available for MBC_ALGO_EGRAPH plans");
     if (pr->n_u < 0 || pr->n_d < 0 || pr->n_u > 6 || pr->n_d > 6 || pr->n_u + pr->n_d == 0)
         return fail(ctx, MBC_UNSUPPORTED, "n_u, n_d must be in 0..6 (not both 0)");
     if (pr->n_free < 1 || pr->n_free > 64) return fail(ctx, MBC_INVALID_ARG, "n_free must be in 1..64");
@@ -580,7 +789,8 @@ mbc_status mbc_plan_from_terms(mbc_ctx* ctx, int n_u, int n_d, int64_t n_terms, 
     Range range_("mbc_plan_from_terms");
     if (!ctx) return MBC_INVALID_ARG;
     if (!out || n_terms < 0 || (n_terms && (!sink || !source || !W))) return fail(ctx, MBC_INVALID_ARG, "bad term arrays");
-    if (algo < 0 || algo > 2 || prec < 0 || prec > 1) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
+    if (algo < 0 || algo > 2 || prec < 0 || prec > 2) return fail(ctx, MBC_INVALID_ARG, "bad algorithm or precision");
+    if (prec == MBC_PREC_FP32) return fail(ctx, MBC_UNSUPPORTED, "MBC_PREC_FP32 is available for MBC_ALGO_EGRAPH plans");
     if (algo == MBC_ALGO_EGRAPH) return fail(ctx, MBC_UNSUPPORTED, "MBC_ALGO_EGRAPH needs a factored problem (mbc_plan_create)");
     if (n_u < 0 || n_d < 0 || n_u > 6 || n_d > 6 || n_u + n_d == 0) return fail(ctx, MBC_UNSUPPORTED, "n_u, n_d must be in 0..6");
     mbc_plan* P = new (std::nothrow) mbc_plan();
@@ -761,6 +971,7 @@ mbc_status check_items(mbc_ctx* c, const mbc_work* items, int n_items) {
         const mbc_work& w = items[i];
         if (!w.plan || w.plan->ctx != c) return fail(c, MBC_INVALID_ARG, "item plan of another context");
         if (w.plan->hp.algo != MBC_ALGO_EGRAPH) return fail(c, MBC_UNSUPPORTED, "batched items must use MBC_ALGO_EGRAPH");
+        if (w.plan->hp.prec == MBC_PREC_FP32) return fail(c, MBC_UNSUPPORTED, "batched items must use FP64 or MIXED plans");
         if (w.n_sets < 0 || w.T < 0 || w.V3 < 0) return fail(c, MBC_INVALID_ARG, "negative item size");
         const int64_t ns = (int64_t)w.n_sets * w.T * w.V3;
         if ((ns && (!w.U || !w.D)) || ((int64_t)w.n_sets * w.T && !w.C)) return fail(c, MBC_INVALID_ARG, "null item buffer");
@@ -876,6 +1087,33 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
     return MBC_OK;
 }
 
+mbc_status mbc_plan_set_guard(mbc_plan* P, double threshold) {
+    if (!P) return MBC_INVALID_ARG;
+    if (std::isnan(threshold)) return fail(P->ctx, MBC_INVALID_ARG, "guard threshold is NaN");
+    P->guard = threshold;
+    P->e32.guard = (float)std::min<double>(std::max<double>(threshold, -1.0), 3.0e38);
+    if (std::isinf(threshold) && threshold > 0) P->e32.guard = INFINITY;
+    return MBC_OK;
+}
+
+mbc_status mbc_plan_get_guard(const mbc_plan* P, double* threshold) {
+    if (!P || !threshold) return MBC_INVALID_ARG;
+    *threshold = P->guard;
+    return MBC_OK;
+}
+
+mbc_status mbc_fp32_recomputed(mbc_ctx* c, int64_t* n_sites) {
+    if (!c || !n_sites) return MBC_INVALID_ARG;
+    *n_sites = 0;
+    if (c->device < 0 || !c->counter.p) return MBC_OK;
+    cudaSetDevice(c->device);
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpy(&v, (unsigned int*)c->counter.p + 1, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the recompute count");
+    *n_sites = v;
+    return MBC_OK;
+}
+
 mbc_status mbc_set_schedule(mbc_plan* P, const mbc_schedule* s) {
     if (!P || !s) return MBC_INVALID_ARG;
     const int max_threads = P->hp.algo == MBC_ALGO_EGRAPH ? 384 : 256;
@@ -900,9 +1138,17 @@ mbc_status mbc_autotune(mbc_plan* P, const void* U, const void* D, int64_t n_sit
     if (!U || !D || n_sites <= 0) return fail(c, MBC_INVALID_ARG, "autotune needs fields and a positive site count");
     if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<mbc_schedule> cands;
+    const mbc_schedule orig = P->sched;
+    if (P->hp.prec == MBC_PREC_FP32) {
+        // the FP32 kernel's shape (walkers, leaf batch) is fixed by the plan's shared memory
+        if (best) *best = orig;
+        return MBC_OK;
+    }
+    // candidates: the plan's current (default) schedule first, then the grid of block
+    // sizes x blocks per SM (x sites per unit for the direct sweep)
+    std::vector<mbc_schedule> cands{orig};
     const int smem = P->ed.smem_values * 16 + 1024;
-    for (int th : {128, 256, 320, 384})
+    for (int th : {128, 256, 320, 352, 384})
         for (int bps : {1, 2, 3, 4, 6, 8}) {
             if (th > 256 && P->hp.algo != MBC_ALGO_EGRAPH) continue;
             if (th * bps > 2048) continue;
@@ -910,36 +1156,52 @@ mbc_status mbc_autotune(mbc_plan* P, const void* U, const void* D, int64_t n_sit
             if (P->hp.algo != MBC_ALGO_EGRAPH && bps != 2) continue;
             for (int spu : {1, 4}) {
                 if (P->hp.algo != MBC_ALGO_DIRECT && spu != 1) continue;
-                cands.push_back({th, bps, spu});
+                const mbc_schedule cs{th, bps, spu};
+                if (cs.threads == orig.threads && cs.blocks_per_sm == orig.blocks_per_sm &&
+                    cs.sites_per_unit == orig.sites_per_unit)
+                    continue;
+                cands.push_back(cs);
             }
         }
     Buf C;
     cudaError_t e = cudaMalloc(&C.p, sizeof(double2) * (size_t)n_sites);
     if (e != cudaSuccess) return fail(c, MBC_OOM, "autotune output");
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto done = [&](mbc_status st) {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        cudaFree(C.p);
+        return st;
+    };
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        P->sched = orig;
+        return done(fail(c, MBC_CUDA, "autotune events"));
+    }
     float best_ms = -1.f;
-    mbc_schedule keep = P->sched;
+    mbc_schedule keep = orig;
     for (auto& cand : cands) {
         P->sched = cand;
-        mbc_status st = run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);   // warm-up (and pool growth)
-        if (st != MBC_OK) { cudaFree(C.p); return st; }
+        // warm-up (and pool growth); a candidate that cannot run is skipped
+        mbc_status st = run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);
+        if (st != MBC_OK) {
+            if (st == MBC_CUDA) { P->sched = orig; return done(st); }   // the context may be unusable
+            continue;
+        }
         cudaEventRecord(a, s);
-        for (int r = 0; r < 3; ++r) run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);
+        for (int r = 0; r < 3 && st == MBC_OK; ++r) st = run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);
         cudaEventRecord(b, s);
-        cudaEventSynchronize(b);
+        e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) { P->sched = orig; return done(cuda_fail(c, e, "autotune timing")); }
+        if (st != MBC_OK) continue;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a, b);
         if (best_ms < 0 || ms < best_ms) { best_ms = ms; keep = cand; }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    cudaFree(C.p);
     P->sched = keep;
     c->tune_cache[P->signature] = keep;
     if (best) *best = keep;
-    return MBC_OK;
+    c->err.clear();
+    return done(MBC_OK);
 }
 
 }  // extern "C"

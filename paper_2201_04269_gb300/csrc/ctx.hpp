@@ -37,6 +37,8 @@ struct mbc_ctx {
     int batch_grid = 0, batch_threads = 384;
     // hadron blocks: per-tile partial blocks, projected blocks, tree partials
     mbc::Buf blk_part, blk_F, blk_tree;
+    // FP32 e-graph: one B table per block, the list of sites to recompute
+    mbc::Buf bslot, flags;
 };
 
 namespace mbc {

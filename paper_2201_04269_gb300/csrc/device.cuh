@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "numeric.cuh"
+#include "walk.hpp"
 
 namespace mbc {
 
@@ -107,6 +108,43 @@ struct EgraphDev {
     const uint8_t* leaf_jmask;
 };
 
+// ---------------------------------------------------------------- FP32 e-graph plan
+// Walker programs of one flavour (walk.hpp) with the level tables they use.
+struct WalkDev {
+    int n;                           // minor size
+    int size[7];                     // entries of the level-k table (size[0] = 1)
+    int off[7];                      // offset of level k (0..n-1) in a walker's table stack
+    int pk_off[7];                   // offset of level k's packed words in the staged word array
+    const WalkStep* steps;
+    const int32_t* step_off;         // [walkers + 1]
+    const WalkLeaf* leaves;
+};
+
+// The e-graph plan of the FP32 kernel: the same column trees, G entries and pairs as
+// EgraphDev, arranged for walkers of 128 threads and FP32 values.
+struct Eg32Dev {
+    int flav_a, n_j, real_w;
+    int walkers, lb;                 // walkers per block, leaf batch size of the A flavour
+    int n_rows_b, n_cols_b;          // the B table of a site is n_cols_b x n_rows_b
+    int stack_vals;                  // float2 values of a walker's table stack
+    int leafbuf_vals;                // lb x size_A[n_A]
+    int pk_words;                    // packed Laplace words staged in shared memory (A, then B)
+    const uint32_t* pk;              // their global copy
+    WalkDev A, B;
+    // G entries in sliced-ELL form (slices of 32 B row sets; entry k of lane l of slice s
+    // and free index j at [sell_off[s * n_j + j] + 32 k + l], k < sell_w[s * n_j + j])
+    const int32_t* sell_off;
+    const int32_t* sell_w;
+    const int2* sell;                // real weights: (A row-set index, float weight bits)
+    const int4* sellc;               // complex weights: (A row-set index, re bits, im bits, 0)
+    const int32_t* pair_off;         // [|cols_A| + 1]
+    const int32_t* pair_cb;          // B column set of each pair
+    const float2* pair_cf;           // [pair * n_j + j]: coef_j = sum_j' P_jj' conj(r_j')
+    const uint8_t* leaf_jmask;       // per A leaf: bit j set when a pair of the leaf has coef_j != 0
+    float guard;                     // a site whose error estimate exceeds this is recomputed
+    int smem_bytes;                  // dynamic shared memory of the kernel
+};
+
 // One item of a batched launch: a plan's device view, its fields, where its per-site
 // partials go, and the number of the item's first work unit (site).
 struct BatchItem {
@@ -132,6 +170,17 @@ cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_u
                                 size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values, cudaStream_t s,
                                 int64_t* launches);
 size_t egraph_kslot_bytes(const EgraphDev& d);
+// FP32 e-graph kernel (egraph32.cu): one block per SM, one site per block at a time.
+// Writes every site's partial; sites whose error estimate exceeds d.guard (or is not
+// finite) are appended to flag_list (flag_count counts them) for the double-float
+// kernel to recompute.  bslots: one n_cols_b x n_rows_b float2 table per block.
+cudaError_t launch_egraph32(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int grid,
+                            void* bslots, unsigned int* counter, unsigned int* flag_count, unsigned int* flag_list,
+                            cudaStream_t s, int64_t* launches);
+// The double-float e-graph kernel over a device list of sites (list_n: device count).
+cudaError_t launch_egraph_list(const EgraphDev& d, const double* U, const double* D, Partials out, int threads,
+                               int grid, unsigned int* counter, void* kscratch, const unsigned int* list,
+                               const unsigned int* list_n, cudaStream_t s, int64_t* launches);
 // Sink momentum of the site sum: p in units of 2 pi / L, site x of a slice at
 // (x mod L, (x / L) mod L, x / L^2); p = 0 is the plain sum.
 struct Momentum {

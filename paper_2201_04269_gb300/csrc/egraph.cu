@@ -300,19 +300,23 @@ template <class P>
 __global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* __restrict__ U,
                                                      const double* __restrict__ D, Geometry g, Partials out,
                                                      unsigned int* __restrict__ counter,
-                                                     typename P::V* __restrict__ kscratch) {
+                                                     typename P::V* __restrict__ kscratch,
+                                                     const unsigned int* __restrict__ list,
+                                                     const unsigned int* __restrict__ list_n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * 32];
     __shared__ unsigned int s_unit;
     __shared__ const uint32_t* pk_owner;
     if (threadIdx.x == 0) pk_owner = nullptr;
     typename P::V* K = kscratch + (size_t)blockIdx.x * d.n_cols_b * d.n_rows_b;      // this block's K slot
-    const int64_t n_units = g.n_sites();
+    // every site of the geometry, or (list mode) the sites of a device list
+    const int64_t n_units = list ? (int64_t)*list_n : g.n_sites();
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
         __syncthreads();
-        const int64_t site = s_unit;
-        if (site >= n_units) break;
+        const int64_t unit = s_unit;
+        if (unit >= n_units) break;
+        const int64_t site = list ? (int64_t)list[unit] : unit;
         egraph_site<P>(d, U, D, site, out.part + site, K, smem_raw, red, &pk_owner);
     }
 }
@@ -383,8 +387,26 @@ cudaError_t launch_egraph(const EgraphDev& d, int prec, const double* U, const d
     grid = (int)std::min<int64_t>(units, grid);
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    if (prec == 0) egraph_kernel<FP64><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cd*)kscratch);
-    else egraph_kernel<MIXED><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cdf*)kscratch);
+    if (prec == 0)
+        egraph_kernel<FP64><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cd*)kscratch, nullptr, nullptr);
+    else
+        egraph_kernel<MIXED><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cdf*)kscratch, nullptr, nullptr);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_egraph_list(const EgraphDev& d, const double* U, const double* D, Partials out, int threads,
+                               int grid, unsigned int* counter, void* kscratch, const unsigned int* list,
+                               const unsigned int* list_n, cudaStream_t s, int64_t* launches) {
+    const size_t smem = egraph_smem_bytes(d, 1);
+    cudaError_t e = cudaFuncSetAttribute(egraph_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    // the list's length is known on the device only: the full persistent grid is
+    // launched and blocks without work exit at once
+    egraph_kernel<MIXED><<<grid, threads, smem, s>>>(d, U, D, Geometry{0, 0, 0}, out, counter, (cdf*)kscratch, list,
+                                                     list_n);
     ++*launches;
     return cudaGetLastError();
 }

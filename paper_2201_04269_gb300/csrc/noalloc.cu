@@ -1,19 +1,22 @@
 // noalloc.cu - correlator evaluation that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc at the moment they need a correlator: code that
-// runs while a stream is being captured into a CUDA graph (an allocation there breaks
-// or invalidates the capture), memory-budgeted services whose device memory is carved
-// out up front and must not grow, and hosts that forbid device allocation after start
-// up.  mbc_correlator normally takes its temporaries (the per-block K slots of the
-// e-graph kernel, the per-site partial sums and the work counter) from the context's
-// pool, growing it with cudaMalloc when a call needs more.  This file offers the same
-// e-graph kernel with every temporary taken from one fixed array compiled into the
-// library instead.
+// Some callers cannot call cudaMalloc at the moment they need a correlator: services
+// whose device memory is carved out once at start up and must not grow afterwards (an
+// allocation could fail, or take memory another tenant of the GPU was promised),
+// plug-ins running inside a host application that owns every device allocation, and
+// real-time loops where an allocation's latency and implicit synchronisation are not
+// acceptable.  mbc_correlator normally takes its temporaries (the per-block K slots of
+// the e-graph kernel, the per-site partial sums and the work counter) from the
+// context's pool, growing it with cudaMalloc when a call needs more.  This file offers
+// the same e-graph kernel with every temporary taken from one fixed array compiled into
+// the library instead.
 //
 // The array is a file-scope __device__ variable of MBC_NOALLOC_SCRATCH_BYTES bytes:
 // every GPU that loads this part of the library holds it until the process exits.
 // Its host-side name is not a device address, so the device address is looked up with
-// cudaGetSymbolAddress once per device, on the first call made on that device.
+// cudaGetSymbolAddress once per device, on the first call made on that device, and
+// kept for the life of the process (a device reset invalidates it: after
+// cudaDeviceReset the entry point is not usable again in that process).
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
@@ -66,6 +69,19 @@ extern "C" mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, cons
     const int64_t n_sites = (int64_t)n_sets * T * V3;
     if ((int64_t)n_sets * T > 0 && !C) return fail(MBC_INVALID_ARG, "null output");
     if (n_sites > 0 && (!U || !D)) return fail(MBC_INVALID_ARG, "null propagator field");
+    cudaError_t e = cudaSetDevice(v.device);
+    if (e != cudaSuccess) return fail(MBC_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    // plans whose canonical term set is empty give C = 0 without a kernel (as
+    // mbc_correlator does), whatever the size
+    if (v.empty || n_sites == 0) {
+        if ((int64_t)n_sets * T > 0) {
+            e = cudaMemsetAsync(C, 0, sizeof(double2) * (size_t)n_sets * T, s);
+            if (e != cudaSuccess) return fail(MBC_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+        }
+        v.err->clear();
+        return MBC_OK;
+    }
     // scratch layout: [work counter | per-site partials | K slots]
     const size_t counter_bytes = 256;
     const size_t part_bytes = align256(sizeof(d4) * (size_t)n_sites);
@@ -78,16 +94,6 @@ extern "C" mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, cons
                  "the fixed array holds %zu bytes",
                  (long long)n_sites, need_min, kslot, part_bytes, (size_t)MBC_NOALLOC_SCRATCH_BYTES);
         return fail(MBC_UNSUPPORTED, buf);
-    }
-    cudaError_t e = cudaSetDevice(v.device);
-    if (e != cudaSuccess) return fail(MBC_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-    cudaStream_t s = (cudaStream_t)stream;
-    if (v.empty || n_sites == 0) {
-        if ((int64_t)n_sets * T > 0) {
-            e = cudaMemsetAsync(C, 0, sizeof(double2) * (size_t)n_sets * T, s);
-            if (e != cudaSuccess) return fail(MBC_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-        }
-        return MBC_OK;
     }
     void* base = nullptr;
     e = scratch_address(v.device, &base);
@@ -103,8 +109,9 @@ extern "C" mbc_status mbc_correlator_noalloc(mbc_plan* plan, const void* U, cons
     Geometry g{n_sets, T, V3};
     Partials pt{parts, 1};
     // the work counter is the only scratch that must start at zero (launch_egraph clears
-    // it on the stream); K slots are written before they are read, partials fully written
-    e = launch_egraph(v.ed, v.prec, (const double*)U, (const double*)D, g, pt, v.threads, grid, counter, kscratch, s,
+    // it on the stream); K slots are written before they are read, partials fully written.
+    // MBC_PREC_FP32 plans are evaluated here with the double-float kernel.
+    e = launch_egraph(v.ed, v.prec == MBC_PREC_FP64 ? 0 : 1, (const double*)U, (const double*)D, g, pt, v.threads, grid, counter, kscratch, s,
                       v.launches);
     if (e != cudaSuccess) return fail(MBC_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     e = launch_reduce(pt, g, v.scale, (double2*)C, nullptr, nullptr, s, v.launches);

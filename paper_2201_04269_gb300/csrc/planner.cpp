@@ -838,7 +838,7 @@ std::string check_minor_plan(const MinorPlan& m, const char* which) {
 
 std::string validate_plan(const HostPlan& p) {
     if (p.n_u < 0 || p.n_u > 6 || p.n_d < 0 || p.n_d > 6 || p.n_u + p.n_d == 0) return "plan: n_u, n_d out of range";
-    if (p.algo < 0 || p.algo > 2 || p.prec < 0 || p.prec > 1) return "plan: algorithm or precision out of range";
+    if (p.algo < 0 || p.algo > 2 || p.prec < 0 || p.prec > 2 || (p.prec == 2 && p.algo != 2)) return "plan: algorithm or precision out of range";
     const int nq = p.n_u + p.n_d;
     for (int8_t v : p.snk_idx) if (v < 0 || v > 11) return "plan: sink index outside 0..11";
     for (int8_t v : p.src_idx) if (v < 0 || v > 11) return "plan: source index outside 0..11";

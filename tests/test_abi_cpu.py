@@ -35,7 +35,7 @@ def hctx(abi):
 def header_functions():
     src = open(os.path.join(ROOT, "include", "mbc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mbc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mbc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(abi):

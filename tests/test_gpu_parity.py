@@ -17,7 +17,9 @@ from oracle import operators as oops
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-5}
+TOL = {"fp64": 1e-12, "mixed": 1e-5, "fp32": 1e-5}
+# MBC_PREC_FP32 with its default guard: the correlator C(t) to the 1e-6 target
+FP32_C_TOL = 1e-6
 TIGHT_MIXED = 1e-9
 ALGOS = ("direct", "tree", "egraph")
 
@@ -277,14 +279,41 @@ def test_batch_matches_separate_calls(ctx):
         assert np.array_equal(it["C"].cpu().numpy(), ref)
 
 
-def test_autotune_keeps_results(ctx):
-    U, D = mi.workload_fields("dinucleon_16x32", L=4, T=4)
+def _time_runs(plan, U, D, reps=5):
+    Ud, Dd = dev(U[None]), dev(D[None])
+    C = torch.zeros(1, U.shape[0], dtype=torch.complex128, device="cuda")
+    plan.correlator(Ud, Dd, C)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.correlator(Ud, Dd, C)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def test_autotune_never_slower_than_default(ctx):
+    """The tuner's candidates include the plan's default schedule, so the schedule it keeps
+    is never slower than the default (re-timed here, within 10 % for noise); results are
+    unchanged up to the reduction order, and a rejected call leaves the schedule as it was."""
+    from paper_2201_04269_gb300 import abi
+    U, D = mi.workload_fields("dinucleon_16x32", L=8, T=4)
     plan = ctx.plan_operator("dinucleon_I", "egraph", "mixed")
+    default = abi.mbc_get_schedule(plan.handle)
     C1, _ = run(plan, U[None], D[None])
+    with pytest.raises(abi.MbcError):
+        abi.mbc_autotune(plan.handle, dev(U), dev(D), 0, ctx=ctx.handle)
+    assert abi.mbc_get_schedule(plan.handle) == default
     s = plan.autotune(dev(U), dev(D), U.shape[0] * U.shape[1])
-    assert s["threads"] in (128, 256) and s["blocks_per_sm"] >= 1
+    assert s == abi.mbc_get_schedule(plan.handle)
+    assert s["threads"] % 32 == 0 and 32 <= s["threads"] <= 384 and s["blocks_per_sm"] >= 1
     C2, _ = run(plan, U[None], D[None])
     check(C2, C1, "mixed")
+    t_tuned = _time_runs(plan, U, D)
+    abi.mbc_set_schedule(plan.handle, default["threads"], default["blocks_per_sm"], default["sites_per_unit"])
+    t_default = _time_runs(plan, U, D)
+    assert t_tuned <= 1.10 * t_default, (s, default, t_tuned, t_default)
     plan.destroy()
 
 
@@ -447,3 +476,98 @@ def test_config5_noisy_32x64(ctx, name):
             ref = oracle_sites(name, U[s, ti, xs], D[s, ti, xs])
             check(S64[s, ti, xs], ref, "fp64")
             check(Smx[s, ti, xs], ref, "mixed")
+
+
+# ---------------------------------------------------------------- FP32 arithmetic (MBC_PREC_FP32)
+FP32_CASES = [("proton", "proton_4x8", dict(L=4, T=8)),
+              ("dinucleon_I", "dinucleon_16x32", dict(L=4, T=3)),
+              ("he3_I", "he3_24x48", dict(L=3, t_list=[0, 9, 30])),
+              ("he3_II_s", "he3_24x48", dict(L=3, t_list=[1, 24, 47]))]
+
+
+@pytest.mark.parametrize("name,wl,kw", FP32_CASES)
+def test_fp32_matches_oracle(ctx, name, wl, kw):
+    """Every site against the oracle at the mixed tolerance, C(t) at 1e-6, with the default
+    guard; guard 0 recomputes every site (double-float accuracy) and +inf none."""
+    U, D = mi.workload_fields(wl, **kw)
+    ref = oracle_sites(name, U, D).reshape(U.shape[:2])
+    plan = ctx.plan_operator(name, "egraph", "fp32")
+    C, S = run(plan, U[None], D[None])
+    check(S[0], ref, "fp32")
+    assert relerr(C[0], ref.sum(axis=1)) <= FP32_C_TOL
+    n = U.shape[0] * U.shape[1]
+    assert 0 <= ctx.fp32_recomputed <= n
+    plan.set_guard(0.0)
+    C0, S0 = run(plan, U[None], D[None])
+    assert ctx.fp32_recomputed == n
+    e = relerr(S0[0], ref)
+    assert e <= TIGHT_MIXED, e
+    plan.set_guard(float("inf"))
+    Ci, Si = run(plan, U[None], D[None])
+    assert ctx.fp32_recomputed == 0
+    check(Si[0], ref, "fp32")
+    plan.destroy()
+
+
+def test_fp32_sampled_24x48_and_deterministic(ctx):
+    """3He_II-s on the full 24^3 x 48 lattice in FP32 (the benchmark's launch): sampled sites
+    against the oracle, C(t) against the double-float plan at 1e-6, bit-reproducible."""
+    U, D = mi.workload_fields("he3_24x48")
+    plan = ctx.plan_operator("he3_II_s", "egraph", "fp32")
+    C1, S1 = run(plan, U[None], D[None])
+    k1 = ctx.fp32_recomputed
+    C2, S2 = run(plan, U[None], D[None])
+    assert np.array_equal(C1, C2) and np.array_equal(S1, S2) and ctx.fp32_recomputed == k1
+    assert 0 < k1 < 0.3 * S1.size
+    rng = np.random.default_rng(11)
+    ts = rng.integers(0, 48, size=24)
+    xs = rng.integers(0, 24 ** 3, size=24)
+    ref = oracle_sites("he3_II_s", U[ts, xs], D[ts, xs])
+    check(S1[0][ts, xs], ref, "fp32")
+    pdf = ctx.plan_operator("he3_II_s", "egraph", "mixed")
+    Cd, _ = run(pdf, U[None], D[None])
+    assert relerr(C1, Cd) <= FP32_C_TOL
+    plan.destroy()
+    pdf.destroy()
+
+
+def test_fp32_general_problems(ctx):
+    """Complex weights and projector, two free indices (the complex-weight kernel), 6 x 6
+    minors and a one-flavour problem (no B minors), against the oracle's index-set sum."""
+    from paper_2201_04269_gb300 import abi, Plan
+    for (n_u, n_d, seed) in ((3, 2, 33), (6, 6, 606), (6, 0, 600), (1, 6, 106)):
+        rng = np.random.default_rng(seed)
+
+        def side(n):
+            idx = np.zeros((n, n_u + n_d), np.int8)
+            for t in range(n):
+                idx[t, :n_u] = rng.choice(12, n_u, replace=False)
+                idx[t, n_u:] = rng.choice(12, n_d, replace=False)
+            return idx, rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        si, sw = side(20)
+        ri, rw = side(16)
+        soff, roff = np.array([0, 9, 20]), np.array([0, 7, 16])
+        P = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+        plan = Plan(ctx, abi.mbc_plan_create(ctx.handle, n_u, n_d, si, sw, soff, ri, rw, roff, P, 1.0, "egraph", "fp32"))
+        U, D = mi.workload_fields("proton_4x8", L=2, T=2)
+        C, S = run(plan, U[None], D[None])
+        snk = [(si[soff[j]:soff[j + 1]], sw[soff[j]:soff[j + 1]]) for j in range(2)]
+        src = [(ri[roff[j]:roff[j + 1]], rw[roff[j]:roff[j + 1]]) for j in range(2)]
+        n = n_u + n_d
+        ref = (-1) ** (n * (n - 1) // 2) * onat.direct(n_u, n_d, snk, src, P, U.reshape(-1, 12, 12),
+                                                        D.reshape(-1, 12, 12))
+        check(S[0].ravel(), ref, "fp32")
+        plan.destroy()
+
+
+def test_fp32_vanishing_and_rejections(ctx):
+    from paper_2201_04269_gb300 import abi
+    U, D = mi.workload_fields("dinucleon_16x32", L=2, T=2)
+    plan = ctx.plan_operator("dinucleon_II", "egraph", "fp32")
+    C, S = run(plan, U[None], D[None])
+    assert np.all(C == 0) and np.all(S == 0)
+    plan.destroy()
+    for algo in ("direct", "tree"):
+        with pytest.raises(abi.MbcError) as e:
+            ctx.plan_operator("proton", algo, "fp32")
+        assert e.value.status == 2
