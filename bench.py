@@ -321,7 +321,8 @@ def main():
     ap.add_argument("--algo", default="egraph", choices=["egraph", "tree", "direct", "blocks", "blocks_local"],
                     help="blocks = hadron blocks projected to zero momentum and the block factor tree; "
                          "blocks_local = the block form of the local-sink correlator (FP64)")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--guard", type=float, default=None, help="FP32 error-estimate threshold (default: the plan's)")
     ap.add_argument("--lattice", default=f"{L}x{T}", help="L x T, e.g. 16x32")
     ap.add_argument("--slices", type=int, default=0, help="time slices evaluated (0 = all)")
     ap.add_argument("--sites", type=int, default=0, help="sink sites per slice (0 = all)")
@@ -373,6 +374,8 @@ def main():
     C = torch.zeros(n_sets, n_t, dtype=torch.complex128, device="cuda")
     ctx = Context(local)
     plan = ctx.plan_operator(args.op, args.algo, args.prec)
+    if args.guard is not None:
+        plan.set_guard(args.guard, float("inf") if args.guard == float("inf") else None)
     info = plan.info
     headline = (args.op == OPERATOR and args.algo == "egraph" and args.prec == "mixed" and (Lb, Tb) == (L, T)
                 and args.slices <= 0 and args.sites <= 0 and args.sets == 1 and args.noise is None)
@@ -405,13 +408,15 @@ def main():
     C_mixed = C.cpu().numpy()[0].copy()
     kname = {"egraph": "egraph_kernel", "tree": "minor_table_kernel + tree_walk_kernel",
              "direct": "direct_kernel"}[args.algo] + ("<MIXED>" if args.prec == "mixed" else "<FP64>")
+    if args.prec == "fp32":
+        kname = "egraph32_kernel"
 
     # dominant kernel alone: the e-graph kernel plus its two small reduction kernels
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     flops = info["flops_per_site"] * n_sites
     achieved = flops / (ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops(sm_max) if args.prec == "mixed" else fp64_peak_tflops(sm_max)
+    peak = fp64_peak_tflops(sm_max) if args.prec == "fp64" else fp32_peak_tflops(sm_max)
     tps = recorded_traffic_per_site() if headline else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None if tps is None else tps * n_sites, "kernel": kname,

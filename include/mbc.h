@@ -224,24 +224,30 @@ mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_strea
  * The minors (Laplace steps of the extracted column trees, Sec. 5), the G stage and the
  * pair products run in complex FP32 on each site's propagators scaled by exact powers
  * of two; every thread sums its parts with TwoSum compensation and the site sum is a
- * compensated double sum.  FP32 rounding (2^-24 per operation) reaches the site value
- * amplified by the cancellation of the site sum (the floating-point problem cited in
- * Sec. 1), so every site also gets an error estimate
- *     est = sqrt(sum over the site's (A leaf, B row set) parts of |part|^2) / |C_x|
- * and every site with est > threshold (or a non-finite estimate) is recomputed by the
- * double-float kernel (the arithmetic of MBC_PREC_MIXED) in a second launch on the same
- * stream, before the site sum.  Measured on He-3 workloads, the FP32 error of a site is
- * about 1e-7 x est; the default threshold 3 keeps it below 1e-6.  threshold = +inf
- * recomputes no site (plain FP32), threshold <= 0 recomputes every site.
+ * compensated double sum.  FP32 rounding (2^-24 per operation) reaches the results
+ * amplified by cancellation (the floating-point problem cited in Sec. 1): within a
+ * site's sum, and across the sites of a time slice in C(t).  Two guards decide which
+ * sites the double-float kernel (the arithmetic of MBC_PREC_MIXED) recomputes, in a
+ * second launch on the same stream before the site sum:
+ *  - per site (only when per-site values are returned, site_out != NULL): with
+ *        s_x = sqrt(sum over the site's (A leaf, B row set) parts of |part|^2),
+ *    a site with s_x / |C_x| > site_threshold (or a non-finite value) is recomputed.
+ *    The FP32 error of a site measured about 1e-7 x s_x (median); the default
+ *    threshold 3 keeps per-site errors near or below 1e-6.  +inf recomputes no site,
+ *    <= 0 every site.
+ *  - per time slice (always): the error of C(t) from the FP32 sites is estimated as
+ *    2.5e-7 x sqrt(sum_x s_x^2) (independent rounding errors), and when that exceeds
+ *    slice_tolerance x |C(t)| (with the sink momentum phase, if any) every remaining
+ *    FP32 site of the slice is recomputed.  Default 1e-6; +inf switches it off.
  *
- * mbc_plan_set_guard / mbc_plan_get_guard: the plan's threshold (host call, takes effect
- * for evaluations issued afterwards).  mbc_fp32_recomputed: the number of sites that the
- * last MBC_PREC_FP32 evaluation of this context recomputed (synchronises the device;
- * 0 if none ran).  Results are bit-reproducible for a given plan, threshold, sizes and
- * device.
+ * mbc_plan_set_guard / mbc_plan_get_guard: the plan's site threshold and slice tolerance
+ * (host calls, effective for evaluations issued afterwards).  mbc_fp32_recomputed: the
+ * number of sites that the last MBC_PREC_FP32 evaluation of this context recomputed
+ * (synchronises the device; 0 if none ran).  Results are bit-reproducible for a given
+ * plan, guards, sizes and device.
  * ---------------------------------------------------------------------------------- */
-mbc_status mbc_plan_set_guard(mbc_plan* plan, double threshold);
-mbc_status mbc_plan_get_guard(const mbc_plan* plan, double* threshold);
+mbc_status mbc_plan_set_guard(mbc_plan* plan, double site_threshold, double slice_tolerance);
+mbc_status mbc_plan_get_guard(const mbc_plan* plan, double* site_threshold, double* slice_tolerance);
 mbc_status mbc_fp32_recomputed(mbc_ctx* ctx, int64_t* n_sites);
 
 /* ------------------------------------------------------------------------------------

@@ -144,3 +144,57 @@ def workload_fields(name: str, set_index: int = 0, t_list=None, L=None, T=None):
     U = propagator_field(seed, set_index, 0, T, V3, w["kappa"], w["noise"], t_list)
     D = propagator_field(seed, set_index, 1, T, V3, w["kappa"], w["noise"], t_list)
     return U, D
+
+
+# ------------------------------------------------------------------ the same recipe on the GPU
+# gen.cu implements the recipe above as a CUDA kernel for fields too large to generate on
+# the host; libmbcgen.so is built next to it by build_gpu() (nvcc, sm_103a).
+_GEN_DIR = os.path.dirname(os.path.abspath(__file__))
+_GEN_SO = os.path.join(_GEN_DIR, "libmbcgen.so")
+_GEN = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile gen.cu into libmbcgen.so (skipped when the library is newer than the source)."""
+    import shutil
+    import subprocess
+    src = os.path.join(_GEN_DIR, "gen.cu")
+    if not force and os.path.exists(_GEN_SO) and os.path.getmtime(_GEN_SO) >= os.path.getmtime(src):
+        return _GEN_SO
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    if not os.path.exists(nvcc):
+        nvcc = shutil.which("nvcc") or "nvcc"
+    tmp = _GEN_SO + ".tmp"
+    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared", "-Xcompiler", "-fPIC", src, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{r.stderr}")
+    os.replace(tmp, _GEN_SO)
+    return _GEN_SO
+
+
+def _gen():
+    global _GEN
+    if _GEN is None:
+        import ctypes
+        lib = ctypes.CDLL(build_gpu())
+        lib.mbcgen_fill.restype = ctypes.c_int
+        lib.mbcgen_fill.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_void_p]
+        _GEN = lib
+    return _GEN
+
+
+def fill_device(out_ptr: int, seed: int, set_index: int, flavour: int, V3: int, t_list, kappa: float = 0.5,
+                noise: float | None = None, stream: int = 0) -> None:
+    """Write the field of one (seed, set, flavour) for the listed time slices into device
+    memory at out_ptr: complex double [len(t_list)][V3][12][12] (same recipe as
+    propagator_field; the transcendental functions are the GPU's)."""
+    import ctypes
+    ts = (ctypes.c_int * len(t_list))(*[int(t) for t in t_list])
+    rc = _gen().mbcgen_fill(ctypes.c_void_p(out_ptr), ctypes.c_uint64(seed), ctypes.c_uint64(set_index), flavour,
+                            ts, len(t_list), V3, kappa, -1.0 if noise is None else float(noise),
+                            ctypes.c_void_p(stream))
+    if rc != 0:
+        raise RuntimeError(f"mbcgen_fill failed with CUDA error {rc}")

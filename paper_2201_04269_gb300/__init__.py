@@ -102,13 +102,17 @@ class Plan:
         n_sets, T, V3 = U.shape[:3]
         abi.mbc_correlator_host(self.handle, U, D, n_sets, T, V3, C, stream, self.ctx.handle)
 
-    def set_guard(self, threshold):
-        """Error-estimate threshold of an MBC_PREC_FP32 plan (sites above it are recomputed
-        in double-float arithmetic)."""
-        abi.mbc_plan_set_guard(self.handle, threshold, self.ctx.handle)
+    def set_guard(self, site_threshold=None, slice_tolerance=None):
+        """Guards of an MBC_PREC_FP32 plan: the per-site error-estimate threshold and the
+        relative error tolerance of C(t); sites they flag are recomputed in double-float
+        arithmetic (None keeps the current value)."""
+        cur = self.guard
+        abi.mbc_plan_set_guard(self.handle, cur[0] if site_threshold is None else site_threshold,
+                               cur[1] if slice_tolerance is None else slice_tolerance, self.ctx.handle)
 
     @property
     def guard(self):
+        """(site threshold, slice tolerance)"""
         return abi.mbc_plan_get_guard(self.handle)
 
     def autotune(self, U, D, n_sites, stream=None):

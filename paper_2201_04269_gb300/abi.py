@@ -106,8 +106,8 @@ SIGNATURES = [
     ("mbc_set_schedule", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_schedule)]),
     ("mbc_get_schedule", ctypes.c_int, [c_vp, ctypes.POINTER(mbc_schedule)]),
     ("mbc_launch_count", ctypes.c_int64, [c_vp]),
-    ("mbc_plan_set_guard", ctypes.c_int, [c_vp, ctypes.c_double]),
-    ("mbc_plan_get_guard", ctypes.c_int, [c_vp, c_dp]),
+    ("mbc_plan_set_guard", ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double]),
+    ("mbc_plan_get_guard", ctypes.c_int, [c_vp, c_dp, c_dp]),
     ("mbc_fp32_recomputed", ctypes.c_int, [c_vp, c_i64p]),
     ("mbc_correlator_noalloc", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, c_vp, c_vp]),
     ("mbc_hadron_blocks", ctypes.c_int, [c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp]),
@@ -349,14 +349,14 @@ def mbc_get_schedule(plan):
     return dict(threads=s.threads, blocks_per_sm=s.blocks_per_sm, sites_per_unit=s.sites_per_unit)
 
 
-def mbc_plan_set_guard(plan, threshold, ctx=None):
-    check(load().mbc_plan_set_guard(plan, float(threshold)), ctx)
+def mbc_plan_set_guard(plan, site_threshold, slice_tolerance, ctx=None):
+    check(load().mbc_plan_set_guard(plan, float(site_threshold), float(slice_tolerance)), ctx)
 
 
 def mbc_plan_get_guard(plan):
-    v = ctypes.c_double()
-    check(load().mbc_plan_get_guard(plan, ctypes.byref(v)))
-    return v.value
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(load().mbc_plan_get_guard(plan, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def mbc_fp32_recomputed(ctx):

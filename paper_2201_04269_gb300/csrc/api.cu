@@ -19,8 +19,10 @@
 using namespace mbc;
 
 namespace {
-// Default error-estimate threshold of MBC_PREC_FP32 plans (see include/mbc.h).
+// Default guards of MBC_PREC_FP32 plans (see include/mbc.h): the per-site error-estimate
+// threshold and the relative error tolerance of C(t).
 constexpr double kDefaultGuard = 3.0;
+constexpr double kDefaultSliceTol = 1e-6;
 }
 
 struct mbc_plan {
@@ -34,7 +36,8 @@ struct mbc_plan {
     Eg32Dev e32{};                // FP32 e-graph view (MBC_PREC_FP32 plans)
     mbc_schedule sched{256, 2, 1};
     mbc_schedule sched_df{384, 1, 1};   // the double-float recompute of flagged sites (MBC_PREC_FP32)
-    double guard = kDefaultGuard;
+    double guard = kDefaultGuard;        // per-site error-estimate threshold (MBC_PREC_FP32)
+    double slice_tol = kDefaultSliceTol; // relative error tolerance of C(t) (MBC_PREC_FP32)
     std::string signature;
 };
 
@@ -131,11 +134,12 @@ void minor_dev_offsets(const MinorPlan& m, int upto, int* size, int* off) {
 // ---------------------------------------------------------------- FP32 e-graph arrays
 struct F32Offsets {
     bool used = false;
-    size_t steps[2], step_off[2], leaves[2], pk, sell_off, sell_w, sell, sellc, pair_off, pair_cb, pair_cf, jmask;
+    size_t steps[2], step_off[2], leaves[2], pk, sell_off, sell_w, sell, sellc, sell1, term_off, term2, term4, jmask;
 };
 
 // Walker count and leaf batch size that fit the kernel's shared memory: as many walkers
-// (up to 8, i.e. 1024 threads) and then as large a batch (up to 6) as fit.
+// (up to 6, i.e. 768 threads: the kernel's register budget) and then as large a batch
+// (up to 3: larger batches measured slower) as fit.
 int f32_smem(int W, int LB, int pk_words, int stack_vals, int leaf_size) {
     return 2 * kBlk * 8 + pk_words * 4 + W * (stack_vals + LB * leaf_size) * 8;
 }
@@ -170,8 +174,10 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
     const int leaf_size = v.A.size[nA];
     const int stack_vals = std::max(stack[0], stack[1]);
     int W = 0, LB = 0;
-    for (int w : {8, 4, 2, 1}) {
-        for (int lb = 6; lb >= 1 && !W; --lb)
+    for (int w : {6, 4, 2, 1}) {
+        // (the leaf stage keeps G of every leaf of a batch in registers: one leaf per batch
+        // when more than two free indices are in use)
+        for (int lb = std::min(e.n_j <= 2 ? 3 : 1, kMaxLeafBatch); lb >= 1 && !W; --lb)
             if (f32_smem(w, lb, pk_words, stack_vals, leaf_size) <= 220 * 1024) { W = w; LB = lb; }
         if (W) break;
     }
@@ -194,9 +200,12 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
         }
         costA[l] = c;
     }
+    // blocks per site: two (a cluster sharing one B table) when one table per SM would
+    // take more than half of the 129 MB L2, so that the tables in flight stay resident
+    const int cs = (double)ncb * nrb * 8.0 * 152 > 64.0 * (1 << 20) ? 2 : 1;
     Walks wk[2];
-    std::string err = build_walks(e.A, W, LB, costA, wk[0]);
-    if (err.empty()) err = build_walks(e.B, W, 255, costB, wk[1]);
+    std::string err = build_walks(e.A, cs * W, LB, costA, wk[0]);
+    if (err.empty()) err = build_walks(e.B, cs * W, kMaxLeafBatch, costB, wk[1]);
     if (!err.empty()) return err;
     for (int f = 0; f < 2; ++f) {
         o.steps[f] = b.add(wk[f].steps);
@@ -216,13 +225,23 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
         }
     }
     o.pk = b.add(pk);
-    // G entries in sliced-ELL form (FP32 weights)
-    bool real = true;
-    for (auto& x : e.g_w) real = real && x.imag() == 0.0;
+    // G entries in sliced-ELL form (FP32 weights); 4-byte entries (index | bf16 weight)
+    // when every weight is real with at most 8 significant bits
+    bool real = true, small = true;
+    for (auto& x : e.g_w) {
+        real = real && x.imag() == 0.0;
+        const float f = (float)x.real();
+        uint32_t bits;
+        std::memcpy(&bits, &f, 4);
+        small = small && x.imag() == 0.0 && (double)f == x.real() && (bits & 0xFFFFu) == 0;
+    }
     for (auto& x : e.pair_coef) real = real && x.imag() == 0.0;
+    for (int32_t a : e.g_a) small = small && a < 65536;
+    small = small && real;
     std::vector<int32_t> soff, sw;
     std::vector<int2> sr;
     std::vector<int4> sc;
+    std::vector<uint32_t> s1;
     const int n_slices = (nrb + 31) / 32;
     size_t rec = 0;
     for (int sl = 0; sl < n_slices; ++sl)
@@ -234,7 +253,8 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
             }
             soff.push_back((int32_t)rec);
             sw.push_back(width);
-            if (real) sr.resize(rec + (size_t)width * 32, int2{0, 0});
+            if (small) s1.resize(rec + (size_t)width * 32, 0u);
+            else if (real) sr.resize(rec + (size_t)width * 32, int2{0, 0});
             else sc.resize(rec + (size_t)width * 32, int4{0, 0, 0, 0});
             for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
                 const int it = (sl * 32 + l) * nj + j;
@@ -244,7 +264,8 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
                     int br, bi;
                     std::memcpy(&br, &wr, 4);
                     std::memcpy(&bi, &wi, 4);
-                    if (real) sr[rec + (size_t)k * 32 + l] = int2{a, br};
+                    if (small) s1[rec + (size_t)k * 32 + l] = (uint32_t)a | ((uint32_t)br & 0xFFFF0000u);
+                    else if (real) sr[rec + (size_t)k * 32 + l] = int2{a, br};
                     else sc[rec + (size_t)k * 32 + l] = int4{a, br, bi, 0};
                 }
             }
@@ -254,11 +275,30 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
     o.sell_w = b.add(sw);
     o.sell = b.add(sr);
     o.sellc = b.add(sc);
-    std::vector<float2> cf(e.pair_coef.size());
-    for (size_t q = 0; q < cf.size(); ++q) cf[q] = make_float2((float)e.pair_coef[q].real(), (float)e.pair_coef[q].imag());
-    o.pair_off = b.add(e.pair_off);
-    o.pair_cb = b.add(e.pair_b);
-    o.pair_cf = b.add(cf);
+    o.sell1 = b.add(s1);
+    // pair terms: one per pair and free index with a nonzero coefficient
+    std::vector<int32_t> toff(1, 0);
+    std::vector<int2> t2;
+    std::vector<int4> t4;
+    for (size_t l = 0; l + 1 < e.pair_off.size(); ++l) {
+        for (int q = e.pair_off[l]; q < e.pair_off[l + 1]; ++q)
+            for (int j = 0; j < nj; ++j) {
+                const cplx cf = e.pair_coef[(size_t)q * nj + j];
+                if (cf == 0.0) continue;
+                const float cr = (float)cf.real(), ci = (float)cf.imag();
+                int br, bi;
+                std::memcpy(&br, &cr, 4);
+                std::memcpy(&bi, &ci, 4);
+                const int x = e.pair_b[q] * 4 + j;
+                if (real) t2.push_back(int2{x, br});
+                else t4.push_back(int4{x, br, bi, 0});
+            }
+        toff.push_back((int32_t)(real ? t2.size() : t4.size()));
+    }
+    o.term_off = b.add(toff);
+    o.term2 = b.add(t2);
+    o.term4 = b.add(t4);
+    v.g_small = small ? 1 : 0;
     std::vector<uint8_t> jm(e.A.cols.size(), 0);
     for (size_t l = 0; l < jm.size(); ++l)
         for (int q = e.pair_off[l]; q < e.pair_off[l + 1]; ++q)
@@ -269,6 +309,7 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
     v.n_j = nj;
     v.real_w = real ? 1 : 0;
     v.walkers = W;
+    v.cs = cs;
     v.lb = LB;
     v.n_rows_b = nrb;
     v.n_cols_b = ncb;
@@ -292,9 +333,10 @@ void bind_f32(Eg32Dev& v, void* dev, const F32Offsets& o, float guard) {
     v.sell_w = at<int32_t>(dev, o.sell_w);
     v.sell = at<int2>(dev, o.sell);
     v.sellc = at<int4>(dev, o.sellc);
-    v.pair_off = at<int32_t>(dev, o.pair_off);
-    v.pair_cb = at<int32_t>(dev, o.pair_cb);
-    v.pair_cf = at<float2>(dev, o.pair_cf);
+    v.sell1 = at<uint32_t>(dev, o.sell1);
+    v.term_off = at<int32_t>(dev, o.term_off);
+    v.term2 = at<int2>(dev, o.term2);
+    v.term4 = at<int4>(dev, o.term4);
     v.leaf_jmask = at<uint8_t>(dev, o.jmask);
     v.guard = guard;
 }
@@ -615,17 +657,21 @@ mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int
     } else if (h.prec == MBC_PREC_FP32) {
         // FP32 pass (one block per SM, a B table per block), then the double-float
         // kernel over the sites whose error estimate exceeded the guard
-        const int grid32 = (int)std::min<int64_t>(n_sites, (int64_t)c->sms);
+        const int grid32 = c->sms;
         const int grid_df = (int)std::min<int64_t>(n_sites, (int64_t)c->sms * P->sched_df.blocks_per_sm);
-        st = ensure(c, c->bslot, sizeof(float2) * (size_t)P->e32.n_cols_b * P->e32.n_rows_b * grid32, s);
+        st = ensure(c, c->bslot, sizeof(float2) * (size_t)P->e32.n_cols_b * P->e32.n_rows_b * (grid32 / P->e32.cs), s);
         if (st == MBC_OK) st = ensure(c, c->flags, sizeof(unsigned int) * (size_t)n_sites, s);
+        if (st == MBC_OK) st = ensure(c, c->gscale, sizeof(double) * (size_t)n_sites, s);
         if (st == MBC_OK) st = ensure(c, c->scratch, egraph_kslot_bytes(P->ed) * (size_t)grid_df, s);
         if (st != MBC_OK) return st;
         unsigned int* cnt = (unsigned int*)c->counter.p;
         e = cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned int), s);
         if (e == cudaSuccess)
-            e = launch_egraph32(P->e32, u, d, g, parts.part, grid32, c->bslot.p, cnt, cnt + 1,
-                                (unsigned int*)c->flags.p, s, &c->launches);
+            // the per-site guard protects per-site values and applies only when they are
+            // returned; the slice guard protects C(t)
+            e = launch_egraph32(P->e32, u, d, g, parts.part, grid32, c->bslot.p, cnt + 1, (unsigned int*)c->flags.p,
+                                site_out ? P->e32.guard : INFINITY, P->slice_tol, (double*)c->gscale.p, mom, s,
+                                &c->launches);
         if (e == cudaSuccess)
             e = launch_egraph_list(P->ed, u, d, parts, P->sched_df.threads, grid_df, cnt + 2, c->scratch.p,
                                    (const unsigned int*)c->flags.p, cnt + 1, s, &c->launches);
@@ -708,7 +754,7 @@ void mbc_destroy(mbc_ctx* c) {
     destroy_block_plans(c);
     Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
                    &c->batch_items, &c->batch_parts, &c->batch_k, &c->blk_part, &c->blk_F, &c->blk_tree,
-                   &c->bslot, &c->flags};
+                   &c->bslot, &c->flags, &c->gscale};
     for (Buf* b : bufs) if (b->p) cudaFree(b->p);
     delete c;
 }
@@ -1087,18 +1133,20 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
     return MBC_OK;
 }
 
-mbc_status mbc_plan_set_guard(mbc_plan* P, double threshold) {
+mbc_status mbc_plan_set_guard(mbc_plan* P, double site_threshold, double slice_tolerance) {
     if (!P) return MBC_INVALID_ARG;
-    if (std::isnan(threshold)) return fail(P->ctx, MBC_INVALID_ARG, "guard threshold is NaN");
-    P->guard = threshold;
-    P->e32.guard = (float)std::min<double>(std::max<double>(threshold, -1.0), 3.0e38);
-    if (std::isinf(threshold) && threshold > 0) P->e32.guard = INFINITY;
+    if (std::isnan(site_threshold) || std::isnan(slice_tolerance))
+        return fail(P->ctx, MBC_INVALID_ARG, "guard threshold or tolerance is NaN");
+    P->guard = site_threshold;
+    P->slice_tol = slice_tolerance;
+    P->e32.guard = site_threshold > 3.0e38 ? INFINITY : (float)std::max(site_threshold, -1.0);
     return MBC_OK;
 }
 
-mbc_status mbc_plan_get_guard(const mbc_plan* P, double* threshold) {
-    if (!P || !threshold) return MBC_INVALID_ARG;
-    *threshold = P->guard;
+mbc_status mbc_plan_get_guard(const mbc_plan* P, double* site_threshold, double* slice_tolerance) {
+    if (!P || !site_threshold || !slice_tolerance) return MBC_INVALID_ARG;
+    *site_threshold = P->guard;
+    *slice_tolerance = P->slice_tol;
     return MBC_OK;
 }
 

@@ -37,8 +37,9 @@ struct mbc_ctx {
     int batch_grid = 0, batch_threads = 384;
     // hadron blocks: per-tile partial blocks, projected blocks, tree partials
     mbc::Buf blk_part, blk_F, blk_tree;
-    // FP32 e-graph: one B table per block, the list of sites to recompute
-    mbc::Buf bslot, flags;
+    // FP32 e-graph: one B table per cluster, the list of sites to recompute, the sites'
+    // error scales
+    mbc::Buf bslot, flags, gscale;
 };
 
 namespace mbc {
@@ -52,8 +53,9 @@ mbc_status ensure(mbc_ctx* c, Buf& b, size_t bytes, cudaStream_t s);
 void destroy_block_plans(mbc_ctx* c);
 
 // NVTX range around an ABI call (a no-op unless a profiler is attached): the planner and
-// every evaluation show up by name on a profiler's timeline, and `ncu --nvtx
-// --nvtx-include "mbc_correlator/"` captures only the kernels of that call.
+// every evaluation show up by name on a profiler's timeline, and `ncu --clock-control
+// none --nvtx --nvtx-include "mbc_correlator/"` captures only the kernels of that call
+// (always with --clock-control none on a shared GPU: ncu otherwise locks the clocks).
 struct Range {
     explicit Range(const char* name) { nvtxRangePushA(name); }
     ~Range() { nvtxRangePop(); }

@@ -125,6 +125,7 @@ struct WalkDev {
 struct Eg32Dev {
     int flav_a, n_j, real_w;
     int walkers, lb;                 // walkers per block, leaf batch size of the A flavour
+    int cs;                          // blocks per site (a thread-block cluster when > 1)
     int n_rows_b, n_cols_b;          // the B table of a site is n_cols_b x n_rows_b
     int stack_vals;                  // float2 values of a walker's table stack
     int leafbuf_vals;                // lb x size_A[n_A]
@@ -137,9 +138,15 @@ struct Eg32Dev {
     const int32_t* sell_w;
     const int2* sell;                // real weights: (A row-set index, float weight bits)
     const int4* sellc;               // complex weights: (A row-set index, re bits, im bits, 0)
-    const int32_t* pair_off;         // [|cols_A| + 1]
-    const int32_t* pair_cb;          // B column set of each pair
-    const float2* pair_cf;           // [pair * n_j + j]: coef_j = sum_j' P_jj' conj(r_j')
+    int g_small;                     // every G weight a real number with at most 8 significant
+                                     // bits (a bfloat16) and every A row-set index < 65536:
+    const uint32_t* sell1;           // ... then the entries are (index | bf16 weight << 16)
+    // pair terms, one per pair (C_a, C_b) and free index j with coef_j != 0, coef_j =
+    // sum_j' P_jj' conj(r_j'(C_a, C_b)); the terms of A leaf C_a are [term_off[C_a],
+    // term_off[C_a + 1]); x = 4 C_b + j
+    const int32_t* term_off;         // [|cols_A| + 1]
+    const int2* term2;               // real coefficients: (x, float bits of coef_j)
+    const int4* term4;               // complex coefficients: (x, re bits, im bits, 0)
     const uint8_t* leaf_jmask;       // per A leaf: bit j set when a pair of the leaf has coef_j != 0
     float guard;                     // a site whose error estimate exceeds this is recomputed
     int smem_bytes;                  // dynamic shared memory of the kernel
@@ -170,13 +177,6 @@ cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_u
                                 size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values, cudaStream_t s,
                                 int64_t* launches);
 size_t egraph_kslot_bytes(const EgraphDev& d);
-// FP32 e-graph kernel (egraph32.cu): one block per SM, one site per block at a time.
-// Writes every site's partial; sites whose error estimate exceeds d.guard (or is not
-// finite) are appended to flag_list (flag_count counts them) for the double-float
-// kernel to recompute.  bslots: one n_cols_b x n_rows_b float2 table per block.
-cudaError_t launch_egraph32(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int grid,
-                            void* bslots, unsigned int* counter, unsigned int* flag_count, unsigned int* flag_list,
-                            cudaStream_t s, int64_t* launches);
 // The double-float e-graph kernel over a device list of sites (list_n: device count).
 cudaError_t launch_egraph_list(const EgraphDev& d, const double* U, const double* D, Partials out, int threads,
                                int grid, unsigned int* counter, void* kscratch, const unsigned int* list,
@@ -187,6 +187,16 @@ struct Momentum {
     int L = 1, px = 0, py = 0, pz = 0;
     __host__ __device__ bool nonzero() const { return (px | py | pz) != 0; }
 };
+// FP32 e-graph kernel (egraph32.cu): one block per SM, one site per cluster of d.cs
+// blocks at a time, at most max_grid blocks; then the slice guard (unless slice_tol is
+// +inf).  Writes every site's partial and its error scale (scale, [n_sites] double, 0
+// for a site already listed); sites whose error estimate exceeds site_guard, and the
+// remaining sites of every time slice whose C(t) error estimate exceeds slice_tol |C(t)|,
+// are appended to flag_list (flag_count counts them) for the double-float kernel to
+// recompute.  bslots: one n_cols_b x n_rows_b float2 table per cluster (max_grid / d.cs).
+cudaError_t launch_egraph32(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int max_grid,
+                            void* bslots, unsigned int* flag_count, unsigned int* flag_list, float site_guard,
+                            double slice_tol, double* scale, Momentum mom, cudaStream_t s, int64_t* launches);
 // C[set][t] = scale * sum_x e^{-i 2 pi p.x / L} (sum over chunks of the site's partials);
 // site_out (optional) receives scale * the site values without the phase.
 cudaError_t launch_reduce(Partials in, Geometry g, cd scale, double2* C, double2* site_out, d4* site_tmp,

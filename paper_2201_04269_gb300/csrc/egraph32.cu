@@ -8,9 +8,11 @@
 // K scratch in global memory:
 //  1. the site's 12x12 blocks are scaled by exact powers of two (largest |re|, |im| in
 //     [0.5, 1)) and rounded to FP32 in shared memory;
-//  2. the block's walkers (groups of 128 threads, named barriers) walk their parts of
-//     the B column tree and write every B leaf table det B[:, C_b] to the block's B
-//     table (n_cols_b x n_rows_b FP32 values in global memory, L2 resident);
+//  2. the walkers (groups of 128 threads, named barriers) of the site's block, or of
+//     the d.cs blocks of its thread-block cluster, walk their parts of the B column tree
+//     and write every B leaf table det B[:, C_b] to the site's B table (n_cols_b x
+//     n_rows_b FP32 values in global memory: a cluster shares one, so that the tables
+//     of every site in flight stay in L2);
 //  3. the walkers walk their parts of the A column tree; the children of a level-(n-1)
 //     node are formed in batches that share the parent's values in registers; for each
 //     leaf C_a and B row set R_b a thread forms G_j(C_a, R_b) and the leaf's part
@@ -64,6 +66,48 @@ __device__ __forceinline__ void cacc_add(CAcc& a, float2 x) {
     two_sum_add(a.si, a.ci, x.y);
 }
 
+// Block sum of every thread's compensated complex sum and guard sum: TwoSum merges across
+// each warp in FP32, the warp results in compensated double by thread 0 (fixed order).
+// Results valid in thread 0; red holds 5 doubles per warp.
+__device__ __forceinline__ void block_sum_site(const CAcc& a, float guard, kacc& re, kacc& im, double& gsum,
+                                               double* red) {
+    float sr = a.sr, cr = a.cr, si = a.si, ci = a.ci, g = guard;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float osr = __shfl_down_sync(0xffffffffu, sr, off), ocr = __shfl_down_sync(0xffffffffu, cr, off);
+        const float osi = __shfl_down_sync(0xffffffffu, si, off), oci = __shfl_down_sync(0xffffffffu, ci, off);
+        g = __fadd_rn(g, __shfl_down_sync(0xffffffffu, g, off));
+        cr = __fadd_rn(cr, ocr);
+        two_sum_add(sr, cr, osr);
+        ci = __fadd_rn(ci, oci);
+        two_sum_add(si, ci, osi);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[5 * warp + 0] = sr;
+        red[5 * warp + 1] = cr;
+        red[5 * warp + 2] = si;
+        red[5 * warp + 3] = ci;
+        red[5 * warp + 4] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        kacc r = {0.0, 0.0}, i = {0.0, 0.0};
+        double gg = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            kacc_add(r, red[5 * w + 0]);
+            kacc_add(r, red[5 * w + 1]);
+            kacc_add(i, red[5 * w + 2]);
+            kacc_add(i, red[5 * w + 3]);
+            gg += red[5 * w + 4];
+        }
+        re = r;
+        im = i;
+        gsum = gg;
+    }
+    __syncthreads();
+}
+
 // Stage the site's two 12x12 blocks as FP32 values scaled by exact powers of two (the
 // largest |re|, |im| of each block in [0.5, 1)); entry (r, c) at [r * kLd + c].
 __device__ __forceinline__ void stage_f32(const double* __restrict__ a, const double* __restrict__ b, float2* sa,
@@ -113,26 +157,43 @@ __device__ __forceinline__ void lap_node(const float2* M, const uint32_t* pk, in
 // A batch of leaves sharing one parent table: for every row set e the K parent values
 // (with the row-position signs) are loaded once and reused for each leaf of the batch.
 // Leaf l's table goes to out + l * n (A: shared memory) or, when to_cols, to
-// out + leaf * n (B: the block's B table, column-major by B column set).
+// out + leaf * n (B: the site's B table, column-major by B column set).  A batch holds
+// at most kMaxLeafBatch leaves; their columns, signs and output offsets stay in registers.
+constexpr int kMaxBatch = kMaxLeafBatch;
 template <int K>
 __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, int n, const WalkLeaf* lv,
                                            int nleaf, const float2* parent, float2* out, bool to_cols, int wt) {
+    int col[kMaxBatch], obase[kMaxBatch];
+    unsigned sm[kMaxBatch];
+#pragma unroll
+    for (int l = 0; l < kMaxBatch; ++l) {
+        col[l] = 0;
+        obase[l] = 0;
+        sm[l] = 0u;
+        if (l < nleaf) {
+            const WalkLeaf L = lv[l];
+            col[l] = L.col;
+            sm[l] = L.sign < 0 ? 0x80000000u : 0u;
+            obase[l] = (to_cols ? L.leaf : l) * n;
+        }
+    }
     for (int e = wt; e < n; e += kWalker) {
         float2 p[K];
-        int r[K];
+        const float2* mr[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const uint32_t w = pk[i * n + e];
-            r[i] = (int)(w >> 16) * kLd;
+            mr[i] = M + (int)(w >> 16) * kLd;
             p[i] = flip_bits(parent[w & 0xFFFFu], (i & 1) ? 0x80000000u : 0u);
         }
-        for (int l = 0; l < nleaf; ++l) {
-            const WalkLeaf L = lv[l];
-            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < K; ++i) acc = cfma(acc, M[r[i] + L.col], p[i]);
-            acc = flip_bits(acc, L.sign < 0 ? 0x80000000u : 0u);
-            out[(size_t)(to_cols ? L.leaf : l) * n + e] = acc;
+        for (int l = 0; l < kMaxBatch; ++l) {
+            if (l < nleaf) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < K; ++i) acc = cfma(acc, mr[i][col[l]], p[i]);
+                out[obase[l] + e] = flip_bits(acc, sm[l]);
+            }
         }
     }
 }
@@ -161,68 +222,116 @@ __device__ __forceinline__ void lap_leaves_k(int k, const float2* M, const uint3
     }
 }
 
-// The leaf stage of a batch of A leaves: items (leaf l, B row set b).  Per item: G_j(b)
-// for the free indices the leaf's pairs use, then the leaf's part
-//   sum_pairs (sum_j coef_j G_j(b)) B[b, C_b],
-// added to the thread's compensated sum; |part|^2 goes to the guard sum.
+template <int NJ>
+__device__ __forceinline__ float2 pick(const float2* g, int j) {
+    float2 v = g[0];
+#pragma unroll
+    for (int q = 1; q < NJ; ++q)
+        if (j == q) v = g[q];
+    return v;
+}
+
+__device__ __forceinline__ void add_part(CAcc& acc, float& guard, float2 part) {
+    cacc_add(acc, part);
+    guard = fmaf(part.x, part.x, fmaf(part.y, part.y, guard));
+}
+
+// The leaf stage of a batch of A leaves, row-major: each thread owns B row sets b (b =
+// wt, wt + 128, ...; the 32 rows of a warp form one sliced-ELL slice).  For each of its
+// rows it loads the G entries s_j(a, b) once and applies them to every leaf of the batch,
+//   G_j(C_a, b) = sum_a s_j(a, b) T_{C_a}[a],
+// then for each leaf takes the part
+//   sum over the leaf's pair terms (C_b, j, coef_j) of coef_j G_j(C_a, b) B[b, C_b]
+// (the term loop is the same for the whole walker: uniform loads, no divergence), adds
+// it to its compensated sum and |part|^2 to the guard sum.  MB leaves at most per batch
+// (the host limits batches to one leaf when more than two free indices are in use).
+// The B table is read through L2 only (another block of the cluster may have written it).
 template <bool REAL, int NJ>
 __device__ __forceinline__ void leaf_stage(const Eg32Dev& d, const WalkLeaf* lv, int nleaf, const float2* leafbuf,
                                            int n_e, const float2* __restrict__ bt, CAcc& acc, float& guard, int wt) {
+    constexpr int MB = NJ <= 2 ? kMaxBatch : 1;
     const int n_rb = d.n_rows_b;
-    const int total = nleaf * n_rb;
-    int l = wt / n_rb, b = wt - (wt / n_rb) * n_rb;
-    for (int it = wt; it < total; it += kWalker) {
-        const int leaf = lv[l].leaf;
-        const float2* T = leafbuf + l * n_e;
-        const int jm = __ldg(d.leaf_jmask + leaf);
+    int lid[MB], lq0[MB], lq1[MB];
+    int jm = 0;
+#pragma unroll
+    for (int l = 0; l < MB; ++l) {
+        lid[l] = 0;
+        lq0[l] = 0;
+        lq1[l] = 0;
+        if (l < nleaf) {
+            lid[l] = lv[l].leaf;
+            jm |= __ldg(d.leaf_jmask + lid[l]);
+            lq0[l] = __ldg(d.term_off + lid[l]);
+            lq1[l] = __ldg(d.term_off + lid[l] + 1);
+        }
+    }
+    for (int b = wt; b < n_rb; b += kWalker) {
         const int sl = b >> 5, lane = b & 31;
-        float2 g[NJ];
+        float2 g[MB][NJ];
+#pragma unroll
+        for (int l = 0; l < MB; ++l)
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) g[l][j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-            g[j] = make_float2(0.f, 0.f);
             if (!((jm >> j) & 1)) continue;
             const int o = __ldg(d.sell_off + sl * NJ + j) + lane;
             const int wd = __ldg(d.sell_w + sl * NJ + j);
-            if (REAL) {
-                for (int k = 0; k < wd; ++k) {
+            for (int k = 0; k < wd; ++k) {
+                int a;
+                float2 w;
+                if (REAL && d.g_small) {
+                    const uint32_t rec = __ldg(d.sell1 + o + k * 32);
+                    a = (int)(rec & 0xFFFFu);
+                    w = make_float2(__uint_as_float(rec & 0xFFFF0000u), 0.f);
+                } else if (REAL) {
                     const int2 rec = __ldg(d.sell + o + k * 32);
-                    const float w = __int_as_float(rec.y);
-                    const float2 t = T[rec.x];
-                    g[j].x = fmaf(w, t.x, g[j].x);
-                    g[j].y = fmaf(w, t.y, g[j].y);
-                }
-            } else {
-                for (int k = 0; k < wd; ++k) {
-                    const int4 rec = __ldg(d.sellc + o + k * 32);
-                    g[j] = cfma(g[j], make_float2(__int_as_float(rec.y), __int_as_float(rec.z)), T[rec.x]);
-                }
-            }
-        }
-        const int p0 = __ldg(d.pair_off + leaf), p1 = __ldg(d.pair_off + leaf + 1);
-        float2 part = make_float2(0.f, 0.f);
-        for (int pr = p0; pr < p1; ++pr) {
-            const int cb = __ldg(d.pair_cb + pr);
-            float2 h = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const float2 c = __ldg(d.pair_cf + pr * NJ + j);
-                if (REAL) {
-                    if (c.x != 0.f) {
-                        h.x = fmaf(c.x, g[j].x, h.x);
-                        h.y = fmaf(c.x, g[j].y, h.y);
-                    }
+                    a = rec.x;
+                    w = make_float2(__int_as_float(rec.y), 0.f);
                 } else {
-                    h = cfma(h, c, g[j]);
+                    const int4 rec = __ldg(d.sellc + o + k * 32);
+                    a = rec.x;
+                    w = make_float2(__int_as_float(rec.y), __int_as_float(rec.z));
+                }
+#pragma unroll
+                for (int l = 0; l < MB; ++l) {
+                    if (l < nleaf) {
+                        const float2 t = leafbuf[l * n_e + a];
+                        if (REAL) {
+                            g[l][j].x = fmaf(w.x, t.x, g[l][j].x);
+                            g[l][j].y = fmaf(w.x, t.y, g[l][j].y);
+                        } else {
+                            g[l][j] = cfma(g[l][j], w, t);
+                        }
+                    }
                 }
             }
-            part = cfma(part, h, bt[(size_t)cb * n_rb + b]);
         }
-        cacc_add(acc, part);
-        guard = fmaf(part.x, part.x, fmaf(part.y, part.y, guard));
-        b += kWalker;
-        while (b >= n_rb) {
-            b -= n_rb;
-            ++l;
+#pragma unroll
+        for (int l = 0; l < MB; ++l) {
+            if (l < nleaf) {
+                float2 part = make_float2(0.f, 0.f);
+                for (int q = lq0[l]; q < lq1[l]; ++q) {
+                    int x;
+                    float2 c;
+                    if (REAL) {
+                        const int2 r = __ldg(d.term2 + q);
+                        x = r.x;
+                        c = make_float2(__int_as_float(r.y), 0.f);
+                    } else {
+                        const int4 r = __ldg(d.term4 + q);
+                        x = r.x;
+                        c = make_float2(__int_as_float(r.y), __int_as_float(r.z));
+                    }
+                    const float2 bv = __ldcg(bt + (x >> 2) * n_rb + b);
+                    const float2 gj = pick<NJ>(g[l], x & 3);
+                    float2 h;
+                    if (REAL) h = make_float2(c.x * gj.x, c.x * gj.y);
+                    else h = cfma(make_float2(0.f, 0.f), c, gj);
+                    part = cfma(part, h, bv);
+                }
+                add_part(acc, guard, part);
+            }
         }
     }
 }
@@ -232,9 +341,9 @@ __device__ __forceinline__ void leaf_stage(const Eg32Dev& d, const WalkLeaf* lv,
 template <bool REAL, int NJ>
 __device__ __forceinline__ void walk(const Eg32Dev& d, const WalkDev& f, bool is_a, const float2* M,
                                      const uint32_t* spk, float2* stack, float2* leafbuf, float2* bt, CAcc& acc,
-                                     float& guard, int w, int wt) {
+                                     float& guard, int gw, int w, int wt) {
     const int n = f.n;
-    const int s0 = __ldg(f.step_off + w), s1 = __ldg(f.step_off + w + 1);
+    const int s0 = __ldg(f.step_off + gw), s1 = __ldg(f.step_off + gw + 1);
     for (int s = s0; s < s1; ++s) {
         const WalkStep st = f.steps[s];
         if (st.level > 0) {
@@ -253,32 +362,54 @@ __device__ __forceinline__ void walk(const Eg32Dev& d, const WalkDev& f, bool is
     }
 }
 
+// Cluster helpers (sm_90+): rank of this block in its cluster, a cluster-wide barrier
+// with release/acquire ordering, and a store to another block's shared memory.
+__device__ __forceinline__ int cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void st_cluster(double* local, int rank, double v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+
+// One site per cluster of d.cs blocks (d.cs == 1: one site per block), sites assigned
+// round robin to clusters.  The cluster's blocks share the site's B table (global
+// memory, one per cluster); their d.walkers walkers each are walkers rank * d.walkers +
+// w of the plan's programs.  With d.cs > 1 every block sends its partial sums to block
+// 0 of the cluster, which combines them in rank order (deterministic).
 template <bool REAL, int NJ>
-__global__ void __launch_bounds__(1024, 1) egraph32_kernel(Eg32Dev d, const double* __restrict__ U,
-                                                           const double* __restrict__ D, Geometry g,
-                                                           d4* __restrict__ part, float2* __restrict__ bslots,
-                                                           unsigned int* __restrict__ counter,
-                                                           unsigned int* __restrict__ flag_count,
-                                                           unsigned int* __restrict__ flag_list) {
+__global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const double* __restrict__ U,
+                                                          const double* __restrict__ D, Geometry g,
+                                                          d4* __restrict__ part, float2* __restrict__ bslots,
+                                                          unsigned int* __restrict__ flag_count,
+                                                          unsigned int* __restrict__ flag_list,
+                                                          float site_guard, double* __restrict__ scale_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[4 * 32];
-    __shared__ unsigned int s_unit;
+    __shared__ double red[5 * 32];
+    __shared__ double xpart[5 * 16];      // block 0 of a cluster: the blocks' (re, im, guard) sums
     float2* sA = reinterpret_cast<float2*>(smem_raw);
     float2* sB = sA + kBlk;
     uint32_t* spk = reinterpret_cast<uint32_t*>(sB + kBlk);
     const int w = threadIdx.x / kWalker, wt = threadIdx.x % kWalker;
+    const int cs = d.cs;
+    const int rank = cs > 1 ? cluster_rank() : 0;
+    const int gw = rank * d.walkers + w;
+    const int64_t cid = blockIdx.x / cs, ncl = gridDim.x / cs;
     float2* stack = reinterpret_cast<float2*>(spk + d.pk_words) + (size_t)w * (d.stack_vals + d.leafbuf_vals);
     float2* leafbuf = stack + d.stack_vals;
-    float2* bt = bslots + (size_t)blockIdx.x * d.n_cols_b * d.n_rows_b;
+    float2* bt = bslots + (size_t)cid * d.n_cols_b * d.n_rows_b;
     for (int i = threadIdx.x; i < d.pk_words; i += blockDim.x) spk[i] = __ldg(d.pk + i);
     if (wt == 0) stack[0] = make_float2(1.f, 0.f);          // level 0: the empty minor
     const int64_t n_units = g.n_sites();
     const int nA = d.A.n, nB = d.B.n;
-    for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
-        __syncthreads();
-        const int64_t site = s_unit;
-        if (site >= n_units) break;
+    for (int64_t site = cid; site < n_units; site += ncl) {
         const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
         const double* mb = (d.flav_a == 0 ? D : U) + site * 288;
         int ea, eb;
@@ -287,60 +418,170 @@ __global__ void __launch_bounds__(1024, 1) egraph32_kernel(Eg32Dev d, const doub
         CAcc acc = {0.f, 0.f, 0.f, 0.f};
         float guard = 0.f;
         if (nB == 0) {
-            if (threadIdx.x == 0) bt[0] = make_float2(1.f, 0.f);
+            if (threadIdx.x == 0 && rank == 0) bt[0] = make_float2(1.f, 0.f);
         } else {
-            walk<REAL, NJ>(d, d.B, false, sB, spk, stack, leafbuf, bt, acc, guard, w, wt);
+            walk<REAL, NJ>(d, d.B, false, sB, spk, stack, leafbuf, bt, acc, guard, gw, w, wt);
         }
         __syncthreads();                                   // the B table is complete
-        walk<REAL, NJ>(d, d.A, true, sA, spk, stack, leafbuf, bt, acc, guard, w, wt);
-        // site value: compensated double block sums of the parts and of |part|^2
-        kacc re, im, gs, gz;
-        block_sum(cd_make((double)acc.sr + (double)acc.cr, (double)acc.si + (double)acc.ci), re, im, red);
-        block_sum(cd_make((double)guard, 0.0), gs, gz, red);
-        if (threadIdx.x == 0) {
-            store_partial(part + site, re, im, ea * nA + eb * nB);
+        if (cs > 1) cluster_sync_all();
+        walk<REAL, NJ>(d, d.A, true, sA, spk, stack, leafbuf, bt, acc, guard, gw, w, wt);
+        // site value: compensated block sums of the parts and of |part|^2
+        kacc re = {0.0, 0.0}, im = {0.0, 0.0}, gs = {0.0, 0.0};
+        block_sum_site(acc, guard, re, im, gs.hi, red);
+        if (cs > 1) {
+            if (threadIdx.x == 0) {
+                st_cluster(xpart + 5 * rank + 0, 0, re.hi);
+                st_cluster(xpart + 5 * rank + 1, 0, re.lo);
+                st_cluster(xpart + 5 * rank + 2, 0, im.hi);
+                st_cluster(xpart + 5 * rank + 3, 0, im.lo);
+                st_cluster(xpart + 5 * rank + 4, 0, gs.hi + gs.lo);
+            }
+            cluster_sync_all();
+            if (rank == 0 && threadIdx.x == 0) {
+                kacc r2 = {0.0, 0.0}, i2 = {0.0, 0.0};
+                double gsum = 0.0;
+                for (int q = 0; q < cs; ++q) {
+                    kacc_merge(r2, kacc{xpart[5 * q + 0], xpart[5 * q + 1]});
+                    kacc_merge(i2, kacc{xpart[5 * q + 2], xpart[5 * q + 3]});
+                    gsum += xpart[5 * q + 4];
+                }
+                re = r2;
+                im = i2;
+                gs = kacc{gsum, 0.0};
+            }
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            const int sc = ea * nA + eb * nB;
+            store_partial(part + site, re, im, sc);
             const double cr = re.hi + re.lo, ci = im.hi + im.lo;
-            const double est = sqrt(gs.hi + gs.lo) / sqrt(cr * cr + ci * ci);
-            if (!(est <= (double)d.guard)) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)site;
+            const double gsum = sqrt(gs.hi + gs.lo);
+            const double est = gsum / sqrt(cr * cr + ci * ci);
+            // per-site guard (when per-site values are returned); a site it sends to the
+            // double-float kernel has no FP32 error left for the slice guard
+            const bool flag = !(est <= (double)site_guard) || !isfinite(gsum);
+            if (flag) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)site;
+            scale_out[site] = flag ? 0.0 : ldexp(gsum, sc);
         }
     }
 }
 
+// The slice guard: one block per (set, t).  The FP32 error of C(t) is estimated as
+//   err(t) = kSliceErr * sqrt(sum_x s_x^2),   s_x = sqrt(sum |part|^2) of site x,
+// (the sites' rounding errors add like independent random numbers; kSliceErr is the
+// ratio of a site's FP32 error to s_x, measured about 1e-7 typical and 1.5e-7 rms on the
+// He-3 workloads, taken with margin), and when err(t) > tol |C(t)| every site of the
+// slice that is not recomputed already is appended to the recompute list.  C(t) here
+// is the FP32 estimate with the momentum phase of the site sum.
+constexpr double kSliceErr = 2.5e-7;
+__global__ void slice_guard_kernel(const d4* __restrict__ part, const double* __restrict__ scale, int64_t V3,
+                                   Momentum mom, double tol, unsigned int* __restrict__ flag_count,
+                                   unsigned int* __restrict__ flag_list) {
+    __shared__ double red[4 * 32];
+    __shared__ int s_flag;
+    const int64_t st = blockIdx.x;
+    double re = 0.0, im = 0.0, m = 0.0;
+    for (int64_t x = threadIdx.x; x < V3; x += blockDim.x) {
+        const d4 v = part[st * V3 + x];
+        double vr = v.x + v.y, vi = v.z + v.w;
+        if (mom.nonzero()) {
+            const int64_t L = mom.L;
+            int64_t k = ((int64_t)mom.px * (x % L) + (int64_t)mom.py * ((x / L) % L) + (int64_t)mom.pz * (x / (L * L))) % L;
+            if (k < 0) k += L;
+            double sn, cs;
+            sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
+            const double tr = vr * cs - vi * sn;
+            vi = vr * sn + vi * cs;
+            vr = tr;
+        }
+        re += vr;
+        im += vi;
+        m = fmax(m, scale[st * V3 + x]);
+    }
+    kacc kr, ki;
+    block_sum(cd_make(re, im), kr, ki, red);          // valid in thread 0
+    m = block_max(m, red);
+    double q = 0.0;
+    if (m > 0.0)
+        for (int64_t x = threadIdx.x; x < V3; x += blockDim.x) {
+            const double r = scale[st * V3 + x] / m;
+            q += r * r;
+        }
+    kacc kq, kz;
+    block_sum(cd_make(q, 0.0), kq, kz, red);
+    if (threadIdx.x == 0) {
+        const double cr = kr.hi + kr.lo, ci = ki.hi + ki.lo;
+        const double err = kSliceErr * m * sqrt(kq.hi + kq.lo);
+        s_flag = m > 0.0 && !(err <= tol * sqrt(cr * cr + ci * ci));
+    }
+    __syncthreads();
+    if (s_flag)
+        for (int64_t x = threadIdx.x; x < V3; x += blockDim.x)
+            if (scale[st * V3 + x] > 0.0) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)(st * V3 + x);
+}
+
 template <bool REAL, int NJ>
-cudaError_t launch_t(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int grid, void* bslots,
-                     unsigned int* counter, unsigned int* flag_count, unsigned int* flag_list, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(egraph32_kernel<REAL, NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         d.smem_bytes);
+cudaError_t launch_t(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int max_grid,
+                     void* bslots, unsigned int* flag_count, unsigned int* flag_list, float site_guard,
+                     double* scale_out, cudaStream_t s) {
+    auto kern = egraph32_kernel<REAL, NJ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_bytes);
     if (e != cudaSuccess) return e;
-    egraph32_kernel<REAL, NJ><<<grid, d.walkers * kWalker, d.smem_bytes, s>>>(d, U, D, g, part, (float2*)bslots,
-                                                                             counter, flag_count, flag_list);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(d.walkers * kWalker);
+    cfg.dynamicSmemBytes = d.smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = d.cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // as many clusters as can be resident at once (at most one per site)
+    int clusters = max_grid / d.cs;
+    if (d.cs > 1) {
+        cfg.gridDim = dim3(d.cs * clusters);
+        int active = 0;
+        e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (active < 1) return cudaErrorInvalidConfiguration;
+        clusters = std::min(clusters, active);
+    }
+    clusters = (int)std::max<int64_t>(1, std::min<int64_t>(clusters, g.n_sites()));
+    cfg.gridDim = dim3(d.cs * clusters);
+    e = cudaLaunchKernelEx(&cfg, kern, d, U, D, g, part, (float2*)bslots, flag_count, flag_list, site_guard,
+                           scale_out);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_egraph32(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int grid,
-                            void* bslots, unsigned int* counter, unsigned int* flag_count, unsigned int* flag_list,
-                            cudaStream_t s, int64_t* launches) {
-    const int64_t units = g.n_sites();
-    if (units == 0) return cudaSuccess;
-    grid = (int)std::min<int64_t>(units, grid);
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
+cudaError_t launch_egraph32(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int max_grid,
+                            void* bslots, unsigned int* flag_count, unsigned int* flag_list, float site_guard,
+                            double slice_tol, double* scale, Momentum mom, cudaStream_t s, int64_t* launches) {
+    if (g.n_sites() == 0) return cudaSuccess;
+    cudaError_t e;
+#define MBC_E32_ARGS d, U, D, g, part, max_grid, bslots, flag_count, flag_list, site_guard, scale, s
     switch (d.n_j * 2 + (d.real_w ? 1 : 0)) {
-        case 3: e = launch_t<true, 1>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
-        case 5: e = launch_t<true, 2>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
-        case 7: e = launch_t<true, 3>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
-        case 9: e = launch_t<true, 4>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
-        case 2: e = launch_t<false, 1>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
-        case 4: e = launch_t<false, 2>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
-        case 6: e = launch_t<false, 3>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
-        case 8: e = launch_t<false, 4>(d, U, D, g, part, grid, bslots, counter, flag_count, flag_list, s); break;
+        case 3: e = launch_t<true, 1>(MBC_E32_ARGS); break;
+        case 5: e = launch_t<true, 2>(MBC_E32_ARGS); break;
+        case 7: e = launch_t<true, 3>(MBC_E32_ARGS); break;
+        case 9: e = launch_t<true, 4>(MBC_E32_ARGS); break;
+        case 2: e = launch_t<false, 1>(MBC_E32_ARGS); break;
+        case 4: e = launch_t<false, 2>(MBC_E32_ARGS); break;
+        case 6: e = launch_t<false, 3>(MBC_E32_ARGS); break;
+        case 8: e = launch_t<false, 4>(MBC_E32_ARGS); break;
         default: return cudaErrorInvalidValue;
     }
+#undef MBC_E32_ARGS
     if (e != cudaSuccess) return e;
     ++*launches;
-    return cudaSuccess;
+    if (std::isinf(slice_tol) && slice_tol > 0) return cudaSuccess;      // slice guard off
+    slice_guard_kernel<<<(unsigned)((int64_t)g.n_sets * g.T), 256, 0, s>>>(part, scale, g.V3, mom, slice_tol,
+                                                                          flag_count, flag_list);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 }  // namespace mbc

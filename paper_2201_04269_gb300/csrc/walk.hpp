@@ -16,6 +16,9 @@
 
 namespace mbc {
 
+// Largest leaf batch of a walker program (the kernel keeps a batch's leaves in registers).
+constexpr int kMaxLeafBatch = 4;
+
 // One step of a walker program.  level >= 1: compute the level-`level` table of the
 // node that adds column `col` (sign (-1)^q of its position q in the node's column set)
 // from the walker's level-(level-1) table.  nleaf > 0: afterwards, form the leaf tables

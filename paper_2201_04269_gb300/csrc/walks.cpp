@@ -9,7 +9,7 @@ namespace mbc {
 std::string build_walks(const MinorPlan& m, int W, int LB, const std::vector<double>& leaf_cost, Walks& out) {
     out = Walks();
     out.step_off.assign(1, 0);
-    if (W < 1 || LB < 1 || LB > 255) return "walks: bad walker count or batch size";
+    if (W < 1 || LB < 1 || LB > kMaxLeafBatch) return "walks: bad walker count or batch size";
     const int n = m.n;
     if (n == 0) {                                   // no minors: every walker is empty
         out.step_off.assign(W + 1, 0);

@@ -293,11 +293,14 @@ def _time_runs(plan, U, D, reps=5):
     return e0.elapsed_time(e1) / reps
 
 
-def test_autotune_never_slower_than_default(ctx):
+def test_autotune_never_slower_than_default():
     """The tuner's candidates include the plan's default schedule, so the schedule it keeps
     is never slower than the default (re-timed here, within 10 % for noise); results are
-    unchanged up to the reduction order, and a rejected call leaves the schedule as it was."""
-    from paper_2201_04269_gb300 import abi
+    unchanged up to the reduction order, and a rejected call leaves the schedule as it was.
+    A context of its own: the tuned schedule goes into the context's cache, which later
+    plans of the same operator would pick up."""
+    from paper_2201_04269_gb300 import abi, Context
+    ctx = Context(0)
     U, D = mi.workload_fields("dinucleon_16x32", L=8, T=4)
     plan = ctx.plan_operator("dinucleon_I", "egraph", "mixed")
     default = abi.mbc_get_schedule(plan.handle)
@@ -315,6 +318,7 @@ def test_autotune_never_slower_than_default(ctx):
     t_default = _time_runs(plan, U, D)
     assert t_tuned <= 1.10 * t_default, (s, default, t_tuned, t_default)
     plan.destroy()
+    ctx.close()
 
 
 @pytest.mark.parametrize("algo", ALGOS)
@@ -502,7 +506,7 @@ def test_fp32_matches_oracle(ctx, name, wl, kw):
     assert ctx.fp32_recomputed == n
     e = relerr(S0[0], ref)
     assert e <= TIGHT_MIXED, e
-    plan.set_guard(float("inf"))
+    plan.set_guard(float("inf"), float("inf"))
     Ci, Si = run(plan, U[None], D[None])
     assert ctx.fp32_recomputed == 0
     check(Si[0], ref, "fp32")
@@ -527,6 +531,14 @@ def test_fp32_sampled_24x48_and_deterministic(ctx):
     pdf = ctx.plan_operator("he3_II_s", "egraph", "mixed")
     Cd, _ = run(pdf, U[None], D[None])
     assert relerr(C1, Cd) <= FP32_C_TOL
+    # C only (no per-site values): only the slice guard recomputes sites
+    Ud, Dd = dev(U[None]), dev(D[None])
+    C3 = torch.zeros(1, 48, dtype=torch.complex128, device="cuda")
+    plan.correlator(Ud, Dd, C3)
+    torch.cuda.synchronize()
+    k3 = ctx.fp32_recomputed
+    assert k3 < k1
+    assert relerr(C3.cpu().numpy(), Cd) <= FP32_C_TOL
     plan.destroy()
     pdf.destroy()
 
