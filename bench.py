@@ -2,15 +2,20 @@
 
 One step = one evaluation of the correlator C(t) of the 3He_II-s operator (the stand-in
 for the printed 3He_II, which vanishes identically) over every sink site of a 24^3 x 48
-lattice (663552 sink-site contractions), with the e-graph plan in the mixed (double-float)
-arithmetic: staging, minors, contraction and the site sum, all in the library's kernels.
-Inputs (2 x 1.5 GB of complex double propagators) are resident in HBM and larger than L2.
+lattice (663552 sink-site contractions), with the e-graph plan in the FP32 arithmetic with
+its error guards (MBC_PREC_FP32: complex FP32 minors and contraction, compensated sums,
+the time slices whose estimated C(t) error exceeds 1e-6 recomputed in double-float):
+staging, minors, contraction, guard, recompute and the site sum, all in the library's
+kernels.  Inputs (2 x 1.5 GB of complex double propagators, generated on the GPU by the
+seeded recipe of mbc_inputs) are resident in HBM and larger than L2.
 
-Prints one JSON line (rank 0).  Extra keys: roofline of the dominant kernel, the FP64
-plan on a subset of time slices (same metric) and the mixed-vs-FP64 relative error,
-the oracle timed on the host cores (cpu_baseline), an end-to-end figure through the
-host-buffer entry point, SM clocks sampled during the timed region and the number of
-kernel launches.  ``--impl reference`` times the oracle instead (on a bounded sample).
+Prints one JSON line (rank 0).  Extra keys: the roofline of the dominant kernel (timed
+alone, guards off), the FP64 and double-float plans on a subset of time slices (same
+metric, timed over repeats) with the FP32 C(t) error against the FP64 C(t), per-site
+errors against the oracle on the sampled sites of the CPU baseline, the oracle timed on
+the host cores (cpu_baseline), an end-to-end figure through the host-buffer entry point,
+SM clocks sampled during the timed region and the number of kernel launches.
+``--impl reference`` times the oracle instead (on a bounded sample).
 """
 from __future__ import annotations
 
@@ -58,8 +63,8 @@ def fp64_peak_tflops(sm_mhz):
     return SM_COUNT * FP64_FMA_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-KERNEL_SOURCES = ("egraph.cu", "numeric.cuh", "common.cuh", "device.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "egraph_kernel_he3_II_s_24x48.md")
+KERNEL_SOURCES = ("egraph32.cu", "numeric.cuh", "common.cuh", "device.cuh", "walk.hpp")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "egraph32_kernel_he3_II_s_24x48.md")
 BLOCK_SOURCES = ("blocks.cu", "blocks.cuh", "numeric.cuh", "common.cuh", "device.cuh")
 BLOCK_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "block_kernels_he3_II_s_24x48.md")
 
@@ -96,6 +101,23 @@ def fields(set_index, t_list=None, seed=SEED, kappa=KAPPA, noise=None, lat=None)
     Ls, Ts = lat or (L, T)
     U = mi.propagator_field(seed, set_index, 0, Ts, Ls ** 3, kappa, noise, t_list)
     D = mi.propagator_field(seed, set_index, 1, Ts, Ls ** 3, kappa, noise, t_list)
+    return U, D
+
+
+def device_fields(set_indices, t_list, seed, kappa, noise, Ls):
+    """U, D cuda complex128 [n_sets, n_t, L^3, 12, 12] generated on the GPU by the seeded
+    recipe of mbc_inputs (the same entries as fields(), up to the last bits of the GPU's
+    transcendental functions)."""
+    import torch
+    import mbc_inputs as mi
+    V3 = Ls ** 3
+    U = torch.empty(len(set_indices), len(t_list), V3, 12, 12, dtype=torch.complex128, device="cuda")
+    D = torch.empty_like(U)
+    st = torch.cuda.current_stream().cuda_stream
+    for k, si in enumerate(set_indices):
+        mi.fill_device(U[k].data_ptr(), seed, si, 0, V3, t_list, kappa, noise, st)
+        mi.fill_device(D[k].data_ptr(), seed, si, 1, V3, t_list, kappa, noise, st)
+    torch.cuda.synchronize()
     return U, D
 
 
@@ -175,11 +197,11 @@ def cpu_baseline(n_sites_target=None, seconds=20.0):
     pts = [(int(t), int(rng.integers(L ** 3))) for t in rng.integers(0, T, size=n)]
     U, D = regen(pts)
     t0 = time.perf_counter()
-    plan.site_values(U, D, n_threads=threads)
+    vals = plan.site_values(U, D, n_threads=threads)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} random sink sites of {OPERATOR} {L}^3x{T} (canonical merged form, plain C, "
-                      f"OpenMP over sites), {dt:.1f} s"}, dt
+                      f"OpenMP over sites), {dt:.1f} s"}, dt, (pts, vals)
 
 
 def run_reference(args, rank, world):
@@ -188,7 +210,7 @@ def run_reference(args, rank, world):
     steps = []
     meta = None
     for i in range(args.warmup + args.steps):
-        meta, dt = cpu_baseline(seconds=min(20.0, 100.0 / max(1, args.warmup + args.steps)))
+        meta, dt, _ = cpu_baseline(seconds=min(20.0, 100.0 / max(1, args.warmup + args.steps)))
         if i >= args.warmup:
             steps.append(dt)
     value = meta["value"]
@@ -315,13 +337,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mbc", choices=["mbc", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--fp64-slices", type=int, default=4)
+    ap.add_argument("--fp64-slices", type=int, default=6)
     # other workloads and algorithms (the default is the benchmark's headline configuration)
     ap.add_argument("--op", default=OPERATOR)
     ap.add_argument("--algo", default="egraph", choices=["egraph", "tree", "direct", "blocks", "blocks_local"],
                     help="blocks = hadron blocks projected to zero momentum and the block factor tree; "
                          "blocks_local = the block form of the local-sink correlator (FP64)")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed", "fp64"],
+                    help="fp32 = FP32 with error guards (default), mixed = double-float, fp64")
+    ap.add_argument("--autotune", action="store_true", help="tune the plan's schedule before timing")
     ap.add_argument("--guard", type=float, default=None, help="FP32 error-estimate threshold (default: the plan's)")
     ap.add_argument("--lattice", default=f"{L}x{T}", help="L x T, e.g. 16x32")
     ap.add_argument("--slices", type=int, default=0, help="time slices evaluated (0 = all)")
@@ -356,29 +380,55 @@ def main():
             dist.destroy_process_group()
         return
 
+    run_local(args, rank, world, local)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def timed(fn, reps, stream):
+    """Average ms of reps calls of fn, CUDA events on the stream (one warm-up call first)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_local(args, rank, world, local):
+    """The local-sink correlator (e-graph, tree or direct plan) on the GPU."""
+    import torch
+    import torch.distributed as dist
+    from paper_2201_04269_gb300 import Context, shard
+
+    stream = torch.cuda.current_stream()
     # weak scaling: every rank evaluates its own propagator sets (its own source times)
-    from paper_2201_04269_gb300 import shard
     Lb, Tb = (int(v) for v in args.lattice.split("x"))
     t_list = list(range(Tb)) if args.slices <= 0 else [int(t) for t in np.linspace(0, Tb - 1, args.slices).round()]
     sets = list(shard.local_sets(args.sets * world, rank, world))
-    hs = [fields(si, t_list, args.seed, args.kappa, args.noise, (Lb, Tb)) for si in sets]
-    U_h = np.stack([h[0] for h in hs])
-    D_h = np.stack([h[1] for h in hs])
+    U, D = device_fields(sets, t_list, args.seed, args.kappa, args.noise, Lb)
     if args.sites > 0:
-        U_h, D_h = np.ascontiguousarray(U_h[:, :, :args.sites]), np.ascontiguousarray(D_h[:, :, :args.sites])
-    del hs
-    n_sets, n_t, n_v = U_h.shape[:3]
+        U, D = U[:, :, :args.sites].contiguous(), D[:, :, :args.sites].contiguous()
+    n_sets, n_t, n_v = U.shape[:3]
     n_sites = n_sets * n_t * n_v
-    U = torch.from_numpy(U_h).cuda()
-    D = torch.from_numpy(D_h).cuda()
+    field_bytes = 2 * U.numel() * 16
     C = torch.zeros(n_sets, n_t, dtype=torch.complex128, device="cuda")
     ctx = Context(local)
     plan = ctx.plan_operator(args.op, args.algo, args.prec)
     if args.guard is not None:
         plan.set_guard(args.guard, float("inf") if args.guard == float("inf") else None)
     info = plan.info
-    headline = (args.op == OPERATOR and args.algo == "egraph" and args.prec == "mixed" and (Lb, Tb) == (L, T)
-                and args.slices <= 0 and args.sites <= 0 and args.sets == 1 and args.noise is None)
+    fp32 = args.prec == "fp32"
+    headline = (args.op == OPERATOR and args.algo == "egraph" and args.prec == "fp32" and (Lb, Tb) == (L, T)
+                and args.slices <= 0 and args.sites <= 0 and args.sets == 1 and args.noise is None
+                and args.guard is None)
+    tuned = None
+    if args.autotune and args.algo == "egraph" and not fp32:
+        tuned = plan.autotune(U, D, min(n_sites, 27648), stream=stream)
 
     def step():
         plan.correlator(U, D, C, stream=stream)
@@ -405,127 +455,120 @@ def main():
         dist.barrier()
         ms = float(t.item())
     clocks = clk.summary()
-    C_mixed = C.cpu().numpy()[0].copy()
-    kname = {"egraph": "egraph_kernel", "tree": "minor_table_kernel + tree_walk_kernel",
-             "direct": "direct_kernel"}[args.algo] + ("<MIXED>" if args.prec == "mixed" else "<FP64>")
-    if args.prec == "fp32":
-        kname = "egraph32_kernel"
+    C_main = C.cpu().numpy().copy()
+    recomputed = ctx.fp32_recomputed if fp32 else 0
+    guards = plan.guard if fp32 else None
 
-    # dominant kernel alone: the e-graph kernel plus its two small reduction kernels
+    # the dominant kernel alone: for FP32 plans with both guards off (no recompute, no slice
+    # guard), so that the step is the FP32 kernel and the site sum
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    flops = info["flops_per_site"] * n_sites
-    achieved = flops / (ms * 1e-3) / 1e12
+    if fp32:
+        plan.set_guard(float("inf"), float("inf"))
+        ms_kernel = timed(step, max(1, min(args.steps, 3)), stream)
+        plan.set_guard(*guards)
+        kname = "egraph32_kernel"
+    else:
+        ms_kernel = ms
+        kname = {"egraph": "egraph_kernel", "tree": "minor_table_kernel + tree_walk_kernel",
+                 "direct": "direct_kernel"}[args.algo] + ("<MIXED>" if args.prec == "mixed" else "<FP64>")
+    achieved = info["flops_per_site"] * n_sites / (ms_kernel * 1e-3) / 1e12
     peak = fp64_peak_tflops(sm_max) if args.prec == "fp64" else fp32_peak_tflops(sm_max)
     tps = recorded_traffic_per_site() if headline else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None if tps is None else tps * n_sites, "kernel": kname,
-                "kernel_source_hash": kernel_hash(),
+                "kernel_ms": ms_kernel, "kernel_source_hash": kernel_hash(),
                 "flops_per_site": info["flops_per_site"], "flop_model": "8 flop per complex multiply-add of the plan",
-                "peak_basis": (f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz (derived)"
-                               if args.prec == "mixed" else
-                               f"FP64: {SM_COUNT} SMs x {FP64_FMA_PER_SM} DFMA/cycle x 2 x {sm_max:.0f} MHz (derived)")}
+                "peak_basis": (f"FP64: {SM_COUNT} SMs x {FP64_FMA_PER_SM} DFMA/cycle x 2 x {sm_max:.0f} MHz (derived)"
+                               if args.prec == "fp64" else
+                               f"FP32: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz (derived)")}
 
-    # FP64 plan on a subset of time slices (same metric), and the mixed error against it
-    fp64 = None
-    if args.fp64_slices > 0 and args.prec == "mixed" and args.algo == "egraph":
-        ts = list(np.linspace(0, n_t - 1, min(args.fp64_slices, n_t)).round().astype(int))
-        p64 = ctx.plan_operator(args.op, "egraph", "fp64")
+    # the FP64 and double-float plans on a subset of time slices (same metric), timed over
+    # repeats; the main plan's C(t) against the FP64 C(t) on those slices
+    compare = {}
+    if args.fp64_slices > 0 and args.algo == "egraph" and args.prec != "fp64":
+        ts = sorted(set(np.linspace(0, n_t - 1, min(args.fp64_slices, n_t)).round().astype(int).tolist()))
         Us, Ds = U[:1, ts].contiguous(), D[:1, ts].contiguous()
-        C64 = torch.zeros(1, len(ts), dtype=torch.complex128, device="cuda")
-        p64.correlator(Us, Ds, C64, stream=stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        p64.correlator(Us, Ds, C64, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        c64 = C64.cpu().numpy()[0]
-        err = float(np.max(np.abs(C_mixed[ts] - c64) / np.maximum(np.abs(c64), 1e-300)))
-        n64 = len(ts) * n_v
-        tf64 = p64.info["flops_per_site"] * n64 / (ms64 * 1e-3) / 1e12
-        fp64 = {"value": n64 / (ms64 * 1e-3), "unit": UNIT, "time_slices": [int(t) for t in ts],
-                "tflops": tf64, "frac_fp64_peak": tf64 / fp64_peak_tflops(sm_max),
-                "mixed_speedup": (n_sites / (ms * 1e-3)) / (n64 / (ms64 * 1e-3)),
-                "rel_err_mixed_vs_fp64": err}
-        p64.destroy()
-
-    # the batched form: the same sites as items of one persistent launch (four time-slice
-    # groups per set, mbc_batch), captured once in a CUDA graph and replayed
-    batched = None
-    if headline or args.batched:
-        from paper_2201_04269_gb300 import abi
-        groups = 4 if n_t >= 4 else 1
-        bounds = [int(round(n_t * k / groups)) for k in range(groups + 1)]
-        items = []
-        for si in range(n_sets):
-            for g0, g1 in zip(bounds[:-1], bounds[1:]):
-                items.append({"plan": plan.handle, "U": U[si, g0:g1], "D": D[si, g0:g1], "n_sets": 1,
-                              "T": g1 - g0, "V3": n_v, "C": C[si, g0:g1]})
-        abi.mbc_batch_reserve(ctx.handle, items)
-        ctx.batch(items, stream=stream)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream()
-        l0 = ctx.launches
-        with torch.cuda.graph(graph, stream=cap):
-            ctx.batch(items, stream=torch.cuda.current_stream())
-        per_replay = ctx.launches - l0
-        graph.replay()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            graph.replay()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msb = e0.elapsed_time(e1) / args.steps
-        batched = {"value": world * n_sites / (msb * 1e-3), "unit": UNIT, "ms_per_step": msb, "items": len(items),
-                   "cuda_graph": True, "launches_per_step": per_replay,
-                   "matches_single_launch": bool(np.array_equal(C.cpu().numpy()[0], C_mixed))}
-        del graph
+        n_sub = len(ts) * n_v
+        reps = max(1, min(args.steps, 5))
+        c64 = None
+        for prec in ("fp64", "mixed") if fp32 else ("fp64",):
+            p2 = ctx.plan_operator(args.op, "egraph", prec)
+            Cs = torch.zeros(1, len(ts), dtype=torch.complex128, device="cuda")
+            with Clocks(local) as clk2:
+                ms2 = timed(lambda: p2.correlator(Us, Ds, Cs, stream=stream), reps, stream)
+            cs = Cs.cpu().numpy()[0]
+            tf = p2.info["flops_per_site"] * n_sub / (ms2 * 1e-3) / 1e12
+            entry = {"value": n_sub / (ms2 * 1e-3), "unit": UNIT, "time_slices": ts, "repeats": reps,
+                     "tflops": tf, "clocks_sm_mhz": clk2.summary()["sm_mhz"],
+                     "speedup_of_main": (n_sites / (ms * 1e-3)) / (n_sub / (ms2 * 1e-3))}
+            if prec == "fp64":
+                entry["frac_fp64_peak"] = tf / fp64_peak_tflops(sm_max)
+                c64 = cs
+            compare[prec] = entry
+            p2.destroy()
+        cm = C_main[0][ts]
+        compare["rel_err_vs_fp64"] = {
+            "max_over_t": float(np.max(np.abs(cm - c64) / np.maximum(np.abs(c64), 1e-300))),
+            "normwise": float(np.max(np.abs(cm - c64)) / np.max(np.abs(c64)))}
 
     # end to end through the host-buffer entry point (pinned host memory)
-    U_pin = torch.from_numpy(U_h).pin_memory()
-    D_pin = torch.from_numpy(D_h).pin_memory()
+    U_pin = torch.empty(U.shape, dtype=U.dtype).pin_memory()
+    D_pin = torch.empty(D.shape, dtype=D.dtype).pin_memory()
+    U_pin.copy_(U)
+    D_pin.copy_(D)
     C_pin = torch.zeros(n_sets, n_t, dtype=torch.complex128).pin_memory()
     plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
     t0 = time.perf_counter()
-    e2e_steps = 1
-    for _ in range(e2e_steps):
-        plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
+    e2e_s = time.perf_counter() - t0
     e2e = {"value": world * n_sites / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(U_pin.numel() * 16 * 2),
            "d2h_bytes_per_step": int(C_pin.numel() * 16)}
+    del U_pin, D_pin
 
-    cpu = None
-    if rank == 0 and not args.no_cpu and headline:
-        cpu, _ = cpu_baseline()
+    cpu, accuracy = None, None
+    if rank == 0 and headline and not args.no_cpu:
+        cpu, _, (pts, ref) = cpu_baseline()
+        # per-site values of the headline plan (per-site guard active) on the sampled sites
+        S = torch.zeros(n_sets, n_t, n_v, dtype=torch.complex128, device="cuda")
+        plan.correlator(U, D, C, S, stream=stream)
+        torch.cuda.synchronize()
+        site_recomputed = ctx.fp32_recomputed if fp32 else 0
+        got = np.array([S[0, t, x].item() for t, x in pts])
+        err = np.abs(got - ref) / np.abs(ref)
+        accuracy = {"sites": len(pts), "rel_err_vs_oracle_max": float(err.max()),
+                    "rel_err_vs_oracle_median": float(np.median(err)),
+                    "rel_err_vs_oracle_q99": float(np.quantile(err, 0.99)),
+                    "recomputed_with_site_values": site_recomputed,
+                    "C_matches_C_only_call": bool(np.allclose(C.cpu().numpy(), C_main, rtol=1e-6, atol=0))}
+        del S
 
     if rank == 0:
         metric = METRIC if headline else f"sink-site contractions/sec ({args.op}, {Lb}^3x{Tb}, {args.algo}, {args.prec})"
+        dtype = {"fp32": "f32", "mixed": "f32x2", "fp64": "f64"}[args.prec]
+        config = {"workload": (f"{args.op}" + (" (stand-in for He-3 II)" if args.op == OPERATOR else "") +
+                               f" {Lb}^3x{Tb}" + (f" ({n_t} slices)" if n_t != Tb else "") +
+                               (f" ({n_v} sites/slice)" if n_v != Lb ** 3 else "") +
+                               f", {n_sets} source(s) per GPU, {args.algo} plan, {args.prec}" +
+                               (f", noise {args.noise}, kappa {args.kappa}" if args.noise else "")),
+                  "sites_per_gpu": n_sites,
+                  "l2": f"inputs {field_bytes / 1e9:.2f} GB per GPU" +
+                        (", larger than L2" if field_bytes > 129e6 else ", smaller than L2"),
+                  "canonical_terms": info["canonical_terms"], "index_size": info["index_size"]}
+        if fp32:
+            config["guard"] = {"site_threshold": guards[0], "slice_tolerance": guards[1],
+                               "recomputed_sites_per_step": recomputed,
+                               "recomputed_fraction": recomputed / max(1, n_sites)}
+        if tuned:
+            config["schedule"] = tuned
         line = {"metric": metric, "value": world * n_sites / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if args.prec == "mixed" else "f64",
-                "data": "synthetic",
-                "config": {"workload": (f"{args.op}" + (" (stand-in for He-3 II)" if args.op == OPERATOR else "") +
-                                        f" {Lb}^3x{Tb}" + (f" ({n_t} slices)" if n_t != Tb else "") +
-                                        (f" ({n_v} sites/slice)" if n_v != Lb ** 3 else "") +
-                                        f", {n_sets} source(s) per GPU, {args.algo} plan, {args.prec}" +
-                                        (f", noise {args.noise}, kappa {args.kappa}" if args.noise else "")),
-                           "sites_per_gpu": n_sites,
-                           "l2": f"inputs {2 * U_h.nbytes / 1e9:.2f} GB per GPU" +
-                                 (", larger than L2" if 2 * U_h.nbytes > 129e6 else ", smaller than L2"),
-                           "canonical_terms": info["canonical_terms"], "index_size": info["index_size"]},
-                "roofline": roofline, "fp64": fp64, "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches,
-                "clocks": clocks}
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic (GPU-generated seeded recipe)",
+                "config": config, "roofline": roofline, "compare": compare or None, "accuracy": accuracy,
+                "batched": None, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.destroy()
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

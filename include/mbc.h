@@ -233,8 +233,8 @@ mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_strea
  *        s_x = sqrt(sum over the site's (A leaf, B row set) parts of |part|^2),
  *    a site with s_x / |C_x| > site_threshold (or a non-finite value) is recomputed.
  *    The FP32 error of a site measured about 1e-7 x s_x (median); the default
- *    threshold 3 keeps per-site errors near or below 1e-6.  +inf recomputes no site,
- *    <= 0 every site.
+ *    threshold 2 (about a quarter of the He-3 sites recomputed) kept every per-site
+ *    error of a 97k-site sample below 1e-6.  +inf recomputes no site, <= 0 every site.
  *  - per time slice (always): the error of C(t) from the FP32 sites is estimated as
  *    2.5e-7 x sqrt(sum_x s_x^2) (independent rounding errors), and when that exceeds
  *    slice_tolerance x |C(t)| (with the sink momentum phase, if any) every remaining

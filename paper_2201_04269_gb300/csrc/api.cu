@@ -21,7 +21,7 @@ using namespace mbc;
 namespace {
 // Default guards of MBC_PREC_FP32 plans (see include/mbc.h): the per-site error-estimate
 // threshold and the relative error tolerance of C(t).
-constexpr double kDefaultGuard = 3.0;
+constexpr double kDefaultGuard = 2.0;
 constexpr double kDefaultSliceTol = 1e-6;
 }
 
@@ -289,7 +289,7 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
                 int br, bi;
                 std::memcpy(&br, &cr, 4);
                 std::memcpy(&bi, &ci, 4);
-                const int x = e.pair_b[q] * 4 + j;
+                const int x = (e.pair_b[q] * nrb) * 4 + j;      // B-table offset of column C_b, free index
                 if (real) t2.push_back(int2{x, br});
                 else t4.push_back(int4{x, br, bi, 0});
             }
@@ -754,7 +754,7 @@ void mbc_destroy(mbc_ctx* c) {
     destroy_block_plans(c);
     Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
                    &c->batch_items, &c->batch_parts, &c->batch_k, &c->blk_part, &c->blk_F, &c->blk_tree,
-                   &c->bslot, &c->flags, &c->gscale};
+                   &c->bslot, &c->flags, &c->gscale, &c->batch32_items};
     for (Buf* b : bufs) if (b->p) cudaFree(b->p);
     delete c;
 }
@@ -1017,7 +1017,6 @@ mbc_status check_items(mbc_ctx* c, const mbc_work* items, int n_items) {
         const mbc_work& w = items[i];
         if (!w.plan || w.plan->ctx != c) return fail(c, MBC_INVALID_ARG, "item plan of another context");
         if (w.plan->hp.algo != MBC_ALGO_EGRAPH) return fail(c, MBC_UNSUPPORTED, "batched items must use MBC_ALGO_EGRAPH");
-        if (w.plan->hp.prec == MBC_PREC_FP32) return fail(c, MBC_UNSUPPORTED, "batched items must use FP64 or MIXED plans");
         if (w.n_sets < 0 || w.T < 0 || w.V3 < 0) return fail(c, MBC_INVALID_ARG, "negative item size");
         const int64_t ns = (int64_t)w.n_sets * w.T * w.V3;
         if ((ns && (!w.U || !w.D)) || ((int64_t)w.n_sets * w.T && !w.C)) return fail(c, MBC_INVALID_ARG, "null item buffer");
@@ -1040,7 +1039,7 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
         part_off[i] = total;
         total += (int64_t)items[i].n_sets * items[i].T * items[i].V3;
         kslot = std::max<int64_t>(kslot, (int64_t)items[i].plan->ed.n_cols_b * items[i].plan->ed.n_rows_b);
-        const int pr = items[i].plan->hp.prec;
+        const int pr = items[i].plan->hp.prec == MBC_PREC_FP64 ? 0 : 1;
         smem[pr] = std::max(smem[pr], egraph_smem_bytes(items[i].plan->ed, pr));
     }
     const size_t max_smem = std::max(smem[0], smem[1]);
@@ -1056,7 +1055,8 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
         c->batch_host[pr].clear();
         int64_t units = 0;
         for (int i = 0; i < n_items; ++i) {
-            if (items[i].plan->hp.prec != pr || items[i].plan->hp.terms.empty()) continue;
+            const int ip = items[i].plan->hp.prec == MBC_PREC_FP64 ? 0 : 1;
+            if (ip != pr || items[i].plan->hp.prec == MBC_PREC_FP32 || items[i].plan->hp.terms.empty()) continue;
             BatchItem b;
             b.d = items[i].plan->ed;
             b.U = (const double*)items[i].U;
@@ -1075,9 +1075,87 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
             if (e != cudaSuccess) return cuda_fail(c, e, "item table upload");
         }
     }
+    // FP32 items: one cluster launch over their (item, site) units with their FP32 views,
+    // and their double-float views (same unit numbering) for the recompute
+    c->batch32_host.clear();
+    c->batch32_df_host.clear();
+    c->batch32_units = 0;
+    c->batch32_slices = 0;
+    int64_t units32 = 0, slices32 = 0, bvals = 1;
+    int cs32 = 0, w32 = 0, smem32 = 0, nj32 = 1;
+    bool real32 = true;
+    for (int i = 0; i < n_items; ++i) {
+        const mbc_plan* P = items[i].plan;
+        if (P->hp.prec != MBC_PREC_FP32 || P->hp.terms.empty()) continue;
+        const Eg32Dev& d = P->e32;
+        if (cs32 == 0) { cs32 = d.cs; w32 = d.walkers; }
+        if (d.cs != cs32 || d.walkers != w32)
+            return fail(c, MBC_UNSUPPORTED, "batched MBC_PREC_FP32 items must share the cluster size and walker count");
+        smem32 = std::max(smem32, d.smem_bytes);
+        nj32 = std::max(nj32, d.n_j);
+        real32 = real32 && d.real_w;
+        bvals = std::max<int64_t>(bvals, (int64_t)d.n_cols_b * d.n_rows_b);
+        const int64_t ns = (int64_t)items[i].n_sets * items[i].T * items[i].V3;
+        BatchItem32 b;
+        b.d = d;
+        b.U = (const double*)items[i].U;
+        b.D = (const double*)items[i].D;
+        b.part = (d4*)c->batch_parts.p + part_off[i];
+        b.scale = nullptr;                           // set below, once the buffer is sized
+        b.g = Geometry{items[i].n_sets, items[i].T, items[i].V3};
+        b.unit_begin = units32;
+        b.slice_begin = slices32;
+        b.site_guard = INFINITY;                     // C only: the slice guard protects it
+        b.slice_tol = P->slice_tol;
+        c->batch32_host.push_back(b);
+        BatchItem bd;
+        bd.d = P->ed;
+        bd.U = b.U;
+        bd.D = b.D;
+        bd.part = b.part;
+        bd.unit_begin = units32;
+        c->batch32_df_host.push_back(bd);
+        units32 += ns;
+        slices32 += (int64_t)items[i].n_sets * items[i].T;
+    }
+    if (!c->batch32_host.empty()) {
+        const int clusters = c->sms / cs32;
+        st = ensure(c, c->bslot, sizeof(float2) * (size_t)bvals * clusters, nullptr);
+        if (st == MBC_OK) st = ensure(c, c->flags, sizeof(unsigned int) * (size_t)units32, nullptr);
+        if (st == MBC_OK) st = ensure(c, c->gscale, sizeof(double) * (size_t)units32, nullptr);
+        if (st == MBC_OK) st = ensure(c, c->batch32_items, (sizeof(BatchItem32) + sizeof(BatchItem)) *
+                                                               c->batch32_host.size(), nullptr);
+        if (st != MBC_OK) return st;
+        for (auto& b : c->batch32_host) b.scale = (double*)c->gscale.p + b.unit_begin;
+        const size_t n32 = c->batch32_host.size();
+        cudaError_t e = cudaMemcpy(c->batch32_items.p, c->batch32_host.data(), sizeof(BatchItem32) * n32,
+                                   cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy((unsigned char*)c->batch32_items.p + sizeof(BatchItem32) * n32, c->batch32_df_host.data(),
+                           sizeof(BatchItem) * n32, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "FP32 item table upload");
+        c->batch32_units = units32;
+        c->batch32_slices = slices32;
+        c->batch32_cs = cs32;
+        c->batch32_walkers = w32;
+        c->batch32_smem = smem32;
+        c->batch32_nj = nj32;
+        c->batch32_real = real32;
+        c->batch32_bvals = bvals;
+        size_t smem_df = 0;
+        int threads_df = 32;
+        for (int i = 0; i < n_items; ++i)
+            if (items[i].plan->hp.prec == MBC_PREC_FP32 && !items[i].plan->hp.terms.empty()) {
+                smem_df = std::max(smem_df, egraph_smem_bytes(items[i].plan->ed, 1));
+                threads_df = std::max(threads_df, items[i].plan->sched_df.threads);
+            }
+        c->batch32_df_smem = smem_df;
+        c->batch32_df_threads = std::min(threads_df, 384);
+    }
     // block size: the largest e-graph schedule among the items (a multiple of 32, <= 384)
     int threads = 32;
-    for (int i = 0; i < n_items; ++i) threads = std::max(threads, items[i].plan->sched.threads);
+    for (int i = 0; i < n_items; ++i)
+        if (items[i].plan->hp.prec != MBC_PREC_FP32) threads = std::max(threads, items[i].plan->sched.threads);
     c->batch_threads = std::min(threads, 384);
     c->batch_kslot = kslot;
     c->batch_grid = grid;
@@ -1109,6 +1187,25 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
                                             c->batch_smem[pr], (unsigned int*)c->counter.p, c->batch_k.p,
                                             c->batch_kslot, s, &c->launches);
         if (e != cudaSuccess) return cuda_fail(c, e, "batched kernel launch");
+    }
+    // FP32 items: the FP32 launch and its slice guard, then the double-float recompute of
+    // the units the guard listed
+    if (!c->batch32_host.empty()) {
+        unsigned int* cnt = (unsigned int*)c->counter.p;
+        const size_t n32 = c->batch32_host.size();
+        const BatchItem32* t32 = (const BatchItem32*)c->batch32_items.p;
+        const BatchItem* tdf = (const BatchItem*)((const unsigned char*)c->batch32_items.p + sizeof(BatchItem32) * n32);
+        cudaError_t e = cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess)
+            e = launch_egraph32_batch(t32, (int)n32, c->batch32_units, c->batch32_slices, c->batch32_real,
+                                      c->batch32_nj, c->batch32_cs, c->batch32_walkers, c->batch32_smem, c->sms,
+                                      c->bslot.p, c->batch32_bvals, cnt + 1, (unsigned int*)c->flags.p, s,
+                                      &c->launches);
+        if (e == cudaSuccess)
+            e = launch_egraph_batch_list(tdf, (int)n32, c->batch32_df_threads, c->batch_grid, c->batch32_df_smem,
+                                         cnt + 2, c->batch_k.p, c->batch_kslot, (const unsigned int*)c->flags.p,
+                                         cnt + 1, s, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(c, e, "batched FP32 launch");
     }
     // site sums per item
     int64_t off = 0;

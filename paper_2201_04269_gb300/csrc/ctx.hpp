@@ -40,6 +40,14 @@ struct mbc_ctx {
     // FP32 e-graph: one B table per cluster, the list of sites to recompute, the sites'
     // error scales
     mbc::Buf bslot, flags, gscale;
+    // batched FP32 items: their FP32 and double-float item tables (device) and launch shape
+    mbc::Buf batch32_items;
+    std::vector<mbc::BatchItem32> batch32_host;
+    std::vector<mbc::BatchItem> batch32_df_host;
+    int64_t batch32_units = 0, batch32_slices = 0, batch32_bvals = 0;
+    int batch32_cs = 1, batch32_walkers = 1, batch32_smem = 0, batch32_nj = 1, batch32_df_threads = 384;
+    bool batch32_real = true;
+    size_t batch32_df_smem = 0;
 };
 
 namespace mbc {

@@ -143,13 +143,29 @@ struct Eg32Dev {
     const uint32_t* sell1;           // ... then the entries are (index | bf16 weight << 16)
     // pair terms, one per pair (C_a, C_b) and free index j with coef_j != 0, coef_j =
     // sum_j' P_jj' conj(r_j'(C_a, C_b)); the terms of A leaf C_a are [term_off[C_a],
-    // term_off[C_a + 1]); x = 4 C_b + j
+    // term_off[C_a + 1]); x = 4 (C_b n_rows_b) + j
     const int32_t* term_off;         // [|cols_A| + 1]
     const int2* term2;               // real coefficients: (x, float bits of coef_j)
     const int4* term4;               // complex coefficients: (x, re bits, im bits, 0)
     const uint8_t* leaf_jmask;       // per A leaf: bit j set when a pair of the leaf has coef_j != 0
     float guard;                     // a site whose error estimate exceeds this is recomputed
     int smem_bytes;                  // dynamic shared memory of the kernel
+};
+
+// One item of a batched FP32 launch: the plan's FP32 view, its fields and geometry, where
+// its per-site partials and error scales go, its first work unit and first time slice
+// (numbered item by item), and its guards.
+struct BatchItem32 {
+    Eg32Dev d;
+    const double* U;
+    const double* D;
+    d4* part;
+    double* scale;
+    Geometry g;
+    int64_t unit_begin;
+    int64_t slice_begin;
+    float site_guard;
+    double slice_tol;
 };
 
 // One item of a batched launch: a plan's device view, its fields, where its per-site
@@ -177,6 +193,19 @@ cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_u
                                 size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values, cudaStream_t s,
                                 int64_t* launches);
 size_t egraph_kslot_bytes(const EgraphDev& d);
+// Batched FP32 launch over items (device table) sharing one cluster size, walker count
+// and shared-memory layout size (smem bytes): the FP32 kernel over every (item, site)
+// unit, then the slice guard of every item's time slices (n_slices in all).  Units to
+// recompute go to flag_list.  bslots: one bslot_values float2 table per cluster.
+cudaError_t launch_egraph32_batch(const BatchItem32* items, int n_items, int64_t n_units, int64_t n_slices, bool real,
+                                  int nj, int cs, int walkers, int smem, int max_grid, void* bslots,
+                                  int64_t bslot_values, unsigned int* flag_count, unsigned int* flag_list,
+                                  cudaStream_t s, int64_t* launches);
+// The double-float batched kernel over a device list of units (list_n: device count).
+cudaError_t launch_egraph_batch_list(const BatchItem* items, int n_items, int threads, int grid, size_t smem,
+                                     unsigned int* counter, void* kscratch, int64_t kslot_values,
+                                     const unsigned int* list, const unsigned int* list_n, cudaStream_t s,
+                                     int64_t* launches);
 // The double-float e-graph kernel over a device list of sites (list_n: device count).
 cudaError_t launch_egraph_list(const EgraphDev& d, const double* U, const double* D, Partials out, int threads,
                                int grid, unsigned int* counter, void* kscratch, const unsigned int* list,

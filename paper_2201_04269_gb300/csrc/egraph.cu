@@ -329,18 +329,23 @@ __global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* 
 template <class P>
 __global__ void __launch_bounds__(384, 3) egraph_batch_kernel(const BatchItem* __restrict__ items, int n_items,
                                                            int64_t n_units, unsigned int* __restrict__ counter,
-                                                           typename P::V* __restrict__ kscratch, int64_t kslot_values) {
+                                                           typename P::V* __restrict__ kscratch, int64_t kslot_values,
+                                                           const unsigned int* __restrict__ list,
+                                                           const unsigned int* __restrict__ list_n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * 32];
     __shared__ unsigned int s_unit;
     __shared__ const uint32_t* pk_owner;
     if (threadIdx.x == 0) pk_owner = nullptr;
     typename P::V* K = kscratch + (size_t)blockIdx.x * kslot_values;
+    // every unit, or (list mode) the units of a device list
+    const int64_t n_work = list ? (int64_t)*list_n : n_units;
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1u);
         __syncthreads();
-        const int64_t unit = s_unit;
-        if (unit >= n_units) break;
+        const int64_t work = s_unit;
+        if (work >= n_work) break;
+        const int64_t unit = list ? (int64_t)list[work] : work;
         int lo = 0, hi = n_items - 1;
         while (lo < hi) {                  // last item whose first unit is <= unit
             const int mid = (lo + hi + 1) >> 1;
@@ -367,9 +372,27 @@ cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_u
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     if (prec == 0)
-        egraph_batch_kernel<FP64><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cd*)kscratch, kslot_values);
+        egraph_batch_kernel<FP64><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cd*)kscratch, kslot_values,
+                                                              nullptr, nullptr);
     else
-        egraph_batch_kernel<MIXED><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cdf*)kscratch, kslot_values);
+        egraph_batch_kernel<MIXED><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cdf*)kscratch,
+                                                               kslot_values, nullptr, nullptr);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_egraph_batch_list(const BatchItem* items, int n_items, int threads, int grid, size_t smem,
+                                     unsigned int* counter, void* kscratch, int64_t kslot_values,
+                                     const unsigned int* list, const unsigned int* list_n, cudaStream_t s,
+                                     int64_t* launches) {
+    if (n_items == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(egraph_batch_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    egraph_batch_kernel<MIXED><<<grid, threads, smem, s>>>(items, n_items, 0, counter, (cdf*)kscratch, kslot_values,
+                                                           list, list_n);
     ++*launches;
     return cudaGetLastError();
 }

@@ -236,47 +236,41 @@ __device__ __forceinline__ void add_part(CAcc& acc, float& guard, float2 part) {
     guard = fmaf(part.x, part.x, fmaf(part.y, part.y, guard));
 }
 
-// The leaf stage of a batch of A leaves, row-major: each thread owns B row sets b (b =
+// The leaf stage of a batch of NL A leaves, row-major: each thread owns B row sets b (b =
 // wt, wt + 128, ...; the 32 rows of a warp form one sliced-ELL slice).  For each of its
 // rows it loads the G entries s_j(a, b) once and applies them to every leaf of the batch,
 //   G_j(C_a, b) = sum_a s_j(a, b) T_{C_a}[a],
 // then for each leaf takes the part
 //   sum over the leaf's pair terms (C_b, j, coef_j) of coef_j G_j(C_a, b) B[b, C_b]
 // (the term loop is the same for the whole walker: uniform loads, no divergence), adds
-// it to its compensated sum and |part|^2 to the guard sum.  MB leaves at most per batch
-// (the host limits batches to one leaf when more than two free indices are in use).
+// it to its compensated sum and |part|^2 to the guard sum.  A term is (x, coef) with
+// x = 4 (C_b n_rows_b) + j: the offset of column C_b in the B table and the free index.
 // The B table is read through L2 only (another block of the cluster may have written it).
-template <bool REAL, int NJ>
-__device__ __forceinline__ void leaf_stage(const Eg32Dev& d, const WalkLeaf* lv, int nleaf, const float2* leafbuf,
-                                           int n_e, const float2* __restrict__ bt, CAcc& acc, float& guard, int wt) {
-    constexpr int MB = NJ <= 2 ? kMaxBatch : 1;
+template <bool REAL, int NJ, int NL>
+__device__ __forceinline__ void leaf_stage_n(const Eg32Dev& d, const WalkLeaf* lv, const float2* leafbuf, int n_e,
+                                             const float2* __restrict__ bt, CAcc& acc, float& guard, int wt) {
     const int n_rb = d.n_rows_b;
-    int lid[MB], lq0[MB], lq1[MB];
+    int lq0[NL], lnt[NL];
     int jm = 0;
 #pragma unroll
-    for (int l = 0; l < MB; ++l) {
-        lid[l] = 0;
-        lq0[l] = 0;
-        lq1[l] = 0;
-        if (l < nleaf) {
-            lid[l] = lv[l].leaf;
-            jm |= __ldg(d.leaf_jmask + lid[l]);
-            lq0[l] = __ldg(d.term_off + lid[l]);
-            lq1[l] = __ldg(d.term_off + lid[l] + 1);
-        }
+    for (int l = 0; l < NL; ++l) {
+        const int id = lv[l].leaf;
+        jm |= __ldg(d.leaf_jmask + id);
+        lq0[l] = __ldg(d.term_off + id);
+        lnt[l] = __ldg(d.term_off + id + 1) - lq0[l];
     }
     for (int b = wt; b < n_rb; b += kWalker) {
         const int sl = b >> 5, lane = b & 31;
-        float2 g[MB][NJ];
+        float2 g[NL][NJ];
 #pragma unroll
-        for (int l = 0; l < MB; ++l)
+        for (int l = 0; l < NL; ++l)
 #pragma unroll
             for (int j = 0; j < NJ; ++j) g[l][j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
             if (!((jm >> j) & 1)) continue;
-            const int o = __ldg(d.sell_off + sl * NJ + j) + lane;
-            const int wd = __ldg(d.sell_w + sl * NJ + j);
+            const int o = __ldg(d.sell_off + sl * d.n_j + j) + lane;
+            const int wd = __ldg(d.sell_w + sl * d.n_j + j);
             for (int k = 0; k < wd; ++k) {
                 int a;
                 float2 w;
@@ -293,47 +287,68 @@ __device__ __forceinline__ void leaf_stage(const Eg32Dev& d, const WalkLeaf* lv,
                     a = rec.x;
                     w = make_float2(__int_as_float(rec.y), __int_as_float(rec.z));
                 }
+                const float2* ta = leafbuf + a;
 #pragma unroll
-                for (int l = 0; l < MB; ++l) {
-                    if (l < nleaf) {
-                        const float2 t = leafbuf[l * n_e + a];
-                        if (REAL) {
-                            g[l][j].x = fmaf(w.x, t.x, g[l][j].x);
-                            g[l][j].y = fmaf(w.x, t.y, g[l][j].y);
-                        } else {
-                            g[l][j] = cfma(g[l][j], w, t);
-                        }
+                for (int l = 0; l < NL; ++l) {
+                    const float2 t = ta[l * n_e];
+                    if (REAL) {
+                        g[l][j].x = fmaf(w.x, t.x, g[l][j].x);
+                        g[l][j].y = fmaf(w.x, t.y, g[l][j].y);
+                    } else {
+                        g[l][j] = cfma(g[l][j], w, t);
                     }
                 }
             }
         }
+        const float2* btb = bt + b;
 #pragma unroll
-        for (int l = 0; l < MB; ++l) {
-            if (l < nleaf) {
-                float2 part = make_float2(0.f, 0.f);
-                for (int q = lq0[l]; q < lq1[l]; ++q) {
-                    int x;
-                    float2 c;
-                    if (REAL) {
-                        const int2 r = __ldg(d.term2 + q);
-                        x = r.x;
-                        c = make_float2(__int_as_float(r.y), 0.f);
-                    } else {
-                        const int4 r = __ldg(d.term4 + q);
-                        x = r.x;
-                        c = make_float2(__int_as_float(r.y), __int_as_float(r.z));
+        for (int l = 0; l < NL; ++l) {
+            float2 part = make_float2(0.f, 0.f);
+            const int nt = lnt[l];
+            if (REAL) {
+                // four terms at a time: their records, then their B values, are independent loads
+                const int2* tp = d.term2 + lq0[l];
+#pragma unroll 1
+                for (int q = 0; q < nt; q += 4) {
+                    int2 r[4];
+                    float2 bv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) r[u] = q + u < nt ? __ldg(tp + q + u) : make_int2(0, 0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) bv[u] = __ldcg(btb + (r[u].x >> 2));
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 gj = pick<NJ>(g[l], r[u].x & 3);
+                        const float c = __int_as_float(r[u].y);
+                        part = cfma(part, make_float2(c * gj.x, c * gj.y), bv[u]);
                     }
-                    const float2 bv = __ldcg(bt + (x >> 2) * n_rb + b);
-                    const float2 gj = pick<NJ>(g[l], x & 3);
-                    float2 h;
-                    if (REAL) h = make_float2(c.x * gj.x, c.x * gj.y);
-                    else h = cfma(make_float2(0.f, 0.f), c, gj);
-                    part = cfma(part, h, bv);
                 }
-                add_part(acc, guard, part);
+            } else {
+                const int4* tp = d.term4 + lq0[l];
+#pragma unroll 1
+                for (int q = 0; q < nt; ++q) {
+                    const int4 r = __ldg(tp + q);
+                    const float2 bv = __ldcg(btb + (r.x >> 2));
+                    const float2 gj = pick<NJ>(g[l], r.x & 3);
+                    part = cfma(part, cfma(make_float2(0.f, 0.f), make_float2(__int_as_float(r.y), __int_as_float(r.z)), gj),
+                                bv);
+                }
             }
+            add_part(acc, guard, part);
         }
     }
+}
+
+template <bool REAL, int NJ>
+__device__ __forceinline__ void leaf_stage(const Eg32Dev& d, const WalkLeaf* lv, int nleaf, const float2* leafbuf,
+                                           int n_e, const float2* __restrict__ bt, CAcc& acc, float& guard, int wt) {
+    if (NJ > 2 || nleaf == 1) {         // one leaf at a time (G of more free indices per leaf)
+        for (int l = 0; l < nleaf; ++l) leaf_stage_n<REAL, NJ, 1>(d, lv + l, leafbuf + l * n_e, n_e, bt, acc, guard, wt);
+        return;
+    }
+    if (nleaf == 2) leaf_stage_n<REAL, NJ, NJ <= 2 ? 2 : 1>(d, lv, leafbuf, n_e, bt, acc, guard, wt);
+    else if (nleaf == 3) leaf_stage_n<REAL, NJ, NJ <= 2 ? 3 : 1>(d, lv, leafbuf, n_e, bt, acc, guard, wt);
+    else leaf_stage_n<REAL, NJ, NJ <= 2 ? 4 : 1>(d, lv, leafbuf, n_e, bt, acc, guard, wt);
 }
 
 // Run one flavour's walker program: B (to_cols: leaf tables to the block's B table) or
@@ -379,11 +394,109 @@ __device__ __forceinline__ void st_cluster(double* local, int rank, double v) {
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
 }
 
-// One site per cluster of d.cs blocks (d.cs == 1: one site per block), sites assigned
-// round robin to clusters.  The cluster's blocks share the site's B table (global
-// memory, one per cluster); their d.walkers walkers each are walkers rank * d.walkers +
-// w of the plan's programs.  With d.cs > 1 every block sends its partial sums to block
-// 0 of the cluster, which combines them in rank order (deterministic).
+// Shared memory of the FP32 kernels and the per-block state of a walker.
+struct Site32Smem {
+    float2* sA;
+    float2* sB;
+    uint32_t* spk;
+    float2* stack;
+    float2* leafbuf;
+    double* red;
+    double* xpart;
+};
+
+__device__ __forceinline__ Site32Smem site32_smem(const Eg32Dev& d, unsigned char* raw, double* red, double* xpart) {
+    Site32Smem m;
+    m.sA = reinterpret_cast<float2*>(raw);
+    m.sB = m.sA + kBlk;
+    m.spk = reinterpret_cast<uint32_t*>(m.sB + kBlk);
+    m.stack = reinterpret_cast<float2*>(m.spk + d.pk_words) + (size_t)(threadIdx.x / kWalker) *
+                                                                  (d.stack_vals + d.leafbuf_vals);
+    m.leafbuf = m.stack + d.stack_vals;
+    m.red = red;
+    m.xpart = xpart;
+    return m;
+}
+
+// Copy the plan's packed Laplace words to shared memory and set level 0 of the walker
+// stacks (the empty minor); block-wide barrier before and after.
+__device__ __forceinline__ void site32_stage_plan(const Eg32Dev& d, const Site32Smem& m) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < d.pk_words; i += blockDim.x) m.spk[i] = __ldg(d.pk + i);
+    if (threadIdx.x % kWalker == 0) m.stack[0] = make_float2(1.f, 0.f);
+    __syncthreads();
+}
+
+// One sink site on one block of its cluster (rank), d.cs blocks per site.  The cluster's
+// blocks share the site's B table bt (global memory); their d.walkers walkers each are
+// walkers rank * d.walkers + w of the plan's programs.  With d.cs > 1 every block sends
+// its partial sums to block 0 of the cluster, which combines them in rank order
+// (deterministic).  Block 0 writes the site's partial and error scale and, when the
+// per-site estimate exceeds site_guard, appends `unit` to the recompute list.
+template <bool REAL, int NJ>
+__device__ __forceinline__ void site32(const Eg32Dev& d, const double* __restrict__ U, const double* __restrict__ D,
+                                       int64_t site, int64_t unit, d4* __restrict__ part, double* __restrict__ scale_out,
+                                       float2* __restrict__ bt, const Site32Smem& m, int rank, float site_guard,
+                                       unsigned int* __restrict__ flag_count, unsigned int* __restrict__ flag_list) {
+    const int w = threadIdx.x / kWalker, wt = threadIdx.x % kWalker;
+    const int cs = d.cs;
+    const int gw = rank * d.walkers + w;
+    const int nA = d.A.n, nB = d.B.n;
+    const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
+    const double* mb = (d.flav_a == 0 ? D : U) + site * 288;
+    int ea, eb;
+    stage_f32(ma, mb, m.sA, m.sB, m.red, ea, eb);
+    __syncthreads();
+    CAcc acc = {0.f, 0.f, 0.f, 0.f};
+    float guard = 0.f;
+    if (nB == 0) {
+        if (threadIdx.x == 0 && rank == 0) bt[0] = make_float2(1.f, 0.f);
+    } else {
+        walk<REAL, NJ>(d, d.B, false, m.sB, m.spk, m.stack, m.leafbuf, bt, acc, guard, gw, w, wt);
+    }
+    __syncthreads();                                   // the B table is complete
+    if (cs > 1) cluster_sync_all();
+    walk<REAL, NJ>(d, d.A, true, m.sA, m.spk, m.stack, m.leafbuf, bt, acc, guard, gw, w, wt);
+    // site value: compensated block sums of the parts and of |part|^2
+    kacc re = {0.0, 0.0}, im = {0.0, 0.0}, gs = {0.0, 0.0};
+    block_sum_site(acc, guard, re, im, gs.hi, m.red);
+    if (cs > 1) {
+        if (threadIdx.x == 0) {
+            st_cluster(m.xpart + 5 * rank + 0, 0, re.hi);
+            st_cluster(m.xpart + 5 * rank + 1, 0, re.lo);
+            st_cluster(m.xpart + 5 * rank + 2, 0, im.hi);
+            st_cluster(m.xpart + 5 * rank + 3, 0, im.lo);
+            st_cluster(m.xpart + 5 * rank + 4, 0, gs.hi + gs.lo);
+        }
+        cluster_sync_all();
+        if (rank == 0 && threadIdx.x == 0) {
+            kacc r2 = {0.0, 0.0}, i2 = {0.0, 0.0};
+            double gsum = 0.0;
+            for (int q = 0; q < cs; ++q) {
+                kacc_merge(r2, kacc{m.xpart[5 * q + 0], m.xpart[5 * q + 1]});
+                kacc_merge(i2, kacc{m.xpart[5 * q + 2], m.xpart[5 * q + 3]});
+                gsum += m.xpart[5 * q + 4];
+            }
+            re = r2;
+            im = i2;
+            gs = kacc{gsum, 0.0};
+        }
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        const int sc = ea * nA + eb * nB;
+        store_partial(part + site, re, im, sc);
+        const double cr = re.hi + re.lo, ci = im.hi + im.lo;
+        const double gsum = sqrt(gs.hi + gs.lo);
+        const double est = gsum / sqrt(cr * cr + ci * ci);
+        // per-site guard (when per-site values are returned); a site it sends to the
+        // double-float kernel has no FP32 error left for the slice guard
+        const bool flag = !(est <= (double)site_guard) || !isfinite(gsum);
+        if (flag) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)unit;
+        scale_out[site] = flag ? 0.0 : ldexp(gsum, sc);
+    }
+}
+
+// One plan: sites assigned round robin to the grid's clusters.
 template <bool REAL, int NJ>
 __global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const double* __restrict__ U,
                                                           const double* __restrict__ D, Geometry g,
@@ -394,74 +507,57 @@ __global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const doubl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[5 * 32];
     __shared__ double xpart[5 * 16];      // block 0 of a cluster: the blocks' (re, im, guard) sums
-    float2* sA = reinterpret_cast<float2*>(smem_raw);
-    float2* sB = sA + kBlk;
-    uint32_t* spk = reinterpret_cast<uint32_t*>(sB + kBlk);
-    const int w = threadIdx.x / kWalker, wt = threadIdx.x % kWalker;
-    const int cs = d.cs;
-    const int rank = cs > 1 ? cluster_rank() : 0;
-    const int gw = rank * d.walkers + w;
-    const int64_t cid = blockIdx.x / cs, ncl = gridDim.x / cs;
-    float2* stack = reinterpret_cast<float2*>(spk + d.pk_words) + (size_t)w * (d.stack_vals + d.leafbuf_vals);
-    float2* leafbuf = stack + d.stack_vals;
+    const Site32Smem m = site32_smem(d, smem_raw, red, xpart);
+    const int rank = d.cs > 1 ? cluster_rank() : 0;
+    const int64_t cid = blockIdx.x / d.cs, ncl = gridDim.x / d.cs;
     float2* bt = bslots + (size_t)cid * d.n_cols_b * d.n_rows_b;
-    for (int i = threadIdx.x; i < d.pk_words; i += blockDim.x) spk[i] = __ldg(d.pk + i);
-    if (wt == 0) stack[0] = make_float2(1.f, 0.f);          // level 0: the empty minor
+    site32_stage_plan(d, m);
     const int64_t n_units = g.n_sites();
-    const int nA = d.A.n, nB = d.B.n;
-    for (int64_t site = cid; site < n_units; site += ncl) {
-        const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
-        const double* mb = (d.flav_a == 0 ? D : U) + site * 288;
-        int ea, eb;
-        stage_f32(ma, mb, sA, sB, red, ea, eb);
+    for (int64_t site = cid; site < n_units; site += ncl)
+        site32<REAL, NJ>(d, U, D, site, site, part, scale_out, bt, m, rank, site_guard, flag_count, flag_list);
+}
+
+// Several (plan, fields) items in one launch: units (item, site) numbered item by item,
+// assigned round robin to the grid's clusters.  Every item has this launch's cluster
+// size, walker count, free-index maximum NJ and weight kind.  A block copies the item's
+// plan view to shared memory and stages its packed words when the item changes.
+template <bool REAL, int NJ>
+__global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem32* __restrict__ items, int n_items,
+                                                                int64_t n_units, float2* __restrict__ bslots,
+                                                                int64_t bslot_values,
+                                                                unsigned int* __restrict__ flag_count,
+                                                                unsigned int* __restrict__ flag_list) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[5 * 32];
+    __shared__ double xpart[5 * 16];
+    __shared__ Eg32Dev sd;
+    __shared__ int s_item;
+    const int cs = items[0].d.cs;
+    const int rank = cs > 1 ? cluster_rank() : 0;
+    const int64_t cid = blockIdx.x / cs, ncl = gridDim.x / cs;
+    float2* bt = bslots + (size_t)cid * bslot_values;
+    int cur = -1;
+    for (int64_t unit = cid; unit < n_units; unit += ncl) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n_items - 1;
+            while (lo < hi) {                  // last item whose first unit is <= unit
+                const int mid = (lo + hi + 1) >> 1;
+                if (items[mid].unit_begin <= unit) lo = mid; else hi = mid - 1;
+            }
+            s_item = lo;
+        }
         __syncthreads();
-        CAcc acc = {0.f, 0.f, 0.f, 0.f};
-        float guard = 0.f;
-        if (nB == 0) {
-            if (threadIdx.x == 0 && rank == 0) bt[0] = make_float2(1.f, 0.f);
-        } else {
-            walk<REAL, NJ>(d, d.B, false, sB, spk, stack, leafbuf, bt, acc, guard, gw, w, wt);
+        const int it = s_item;
+        if (it != cur) {
+            if (threadIdx.x == 0) sd = items[it].d;
+            __syncthreads();
+            site32_stage_plan(sd, site32_smem(sd, smem_raw, red, xpart));
+            cur = it;
         }
-        __syncthreads();                                   // the B table is complete
-        if (cs > 1) cluster_sync_all();
-        walk<REAL, NJ>(d, d.A, true, sA, spk, stack, leafbuf, bt, acc, guard, gw, w, wt);
-        // site value: compensated block sums of the parts and of |part|^2
-        kacc re = {0.0, 0.0}, im = {0.0, 0.0}, gs = {0.0, 0.0};
-        block_sum_site(acc, guard, re, im, gs.hi, red);
-        if (cs > 1) {
-            if (threadIdx.x == 0) {
-                st_cluster(xpart + 5 * rank + 0, 0, re.hi);
-                st_cluster(xpart + 5 * rank + 1, 0, re.lo);
-                st_cluster(xpart + 5 * rank + 2, 0, im.hi);
-                st_cluster(xpart + 5 * rank + 3, 0, im.lo);
-                st_cluster(xpart + 5 * rank + 4, 0, gs.hi + gs.lo);
-            }
-            cluster_sync_all();
-            if (rank == 0 && threadIdx.x == 0) {
-                kacc r2 = {0.0, 0.0}, i2 = {0.0, 0.0};
-                double gsum = 0.0;
-                for (int q = 0; q < cs; ++q) {
-                    kacc_merge(r2, kacc{xpart[5 * q + 0], xpart[5 * q + 1]});
-                    kacc_merge(i2, kacc{xpart[5 * q + 2], xpart[5 * q + 3]});
-                    gsum += xpart[5 * q + 4];
-                }
-                re = r2;
-                im = i2;
-                gs = kacc{gsum, 0.0};
-            }
-        }
-        if (rank == 0 && threadIdx.x == 0) {
-            const int sc = ea * nA + eb * nB;
-            store_partial(part + site, re, im, sc);
-            const double cr = re.hi + re.lo, ci = im.hi + im.lo;
-            const double gsum = sqrt(gs.hi + gs.lo);
-            const double est = gsum / sqrt(cr * cr + ci * ci);
-            // per-site guard (when per-site values are returned); a site it sends to the
-            // double-float kernel has no FP32 error left for the slice guard
-            const bool flag = !(est <= (double)site_guard) || !isfinite(gsum);
-            if (flag) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)site;
-            scale_out[site] = flag ? 0.0 : ldexp(gsum, sc);
-        }
+        const BatchItem32& item = items[it];
+        const Site32Smem m = site32_smem(sd, smem_raw, red, xpart);
+        site32<REAL, NJ>(sd, item.U, item.D, unit - item.unit_begin, unit, item.part, item.scale, bt, m, rank,
+                         item.site_guard, flag_count, flag_list);
     }
 }
 
@@ -473,12 +569,10 @@ __global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const doubl
 // slice that is not recomputed already is appended to the recompute list.  C(t) here
 // is the FP32 estimate with the momentum phase of the site sum.
 constexpr double kSliceErr = 2.5e-7;
-__global__ void slice_guard_kernel(const d4* __restrict__ part, const double* __restrict__ scale, int64_t V3,
-                                   Momentum mom, double tol, unsigned int* __restrict__ flag_count,
-                                   unsigned int* __restrict__ flag_list) {
-    __shared__ double red[4 * 32];
-    __shared__ int s_flag;
-    const int64_t st = blockIdx.x;
+__device__ __forceinline__ void slice_guard_body(const d4* __restrict__ part, const double* __restrict__ scale,
+                                                 int64_t st, int64_t V3, Momentum mom, double tol, int64_t unit0,
+                                                 unsigned int* __restrict__ flag_count,
+                                                 unsigned int* __restrict__ flag_list, double* red, int* s_flag) {
     double re = 0.0, im = 0.0, m = 0.0;
     for (int64_t x = threadIdx.x; x < V3; x += blockDim.x) {
         const d4 v = part[st * V3 + x];
@@ -511,48 +605,87 @@ __global__ void slice_guard_kernel(const d4* __restrict__ part, const double* __
     if (threadIdx.x == 0) {
         const double cr = kr.hi + kr.lo, ci = ki.hi + ki.lo;
         const double err = kSliceErr * m * sqrt(kq.hi + kq.lo);
-        s_flag = m > 0.0 && !(err <= tol * sqrt(cr * cr + ci * ci));
+        *s_flag = m > 0.0 && !(err <= tol * sqrt(cr * cr + ci * ci));
     }
     __syncthreads();
-    if (s_flag)
+    if (*s_flag)
         for (int64_t x = threadIdx.x; x < V3; x += blockDim.x)
-            if (scale[st * V3 + x] > 0.0) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)(st * V3 + x);
+            if (scale[st * V3 + x] > 0.0) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)(unit0 + st * V3 + x);
+    __syncthreads();
 }
 
-template <bool REAL, int NJ>
-cudaError_t launch_t(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int max_grid,
-                     void* bslots, unsigned int* flag_count, unsigned int* flag_list, float site_guard,
-                     double* scale_out, cudaStream_t s) {
-    auto kern = egraph32_kernel<REAL, NJ>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, d.smem_bytes);
+__global__ void slice_guard_kernel(const d4* __restrict__ part, const double* __restrict__ scale, int64_t V3,
+                                   Momentum mom, double tol, unsigned int* __restrict__ flag_count,
+                                   unsigned int* __restrict__ flag_list) {
+    __shared__ double red[4 * 32];
+    __shared__ int s_flag;
+    slice_guard_body(part, scale, blockIdx.x, V3, mom, tol, 0, flag_count, flag_list, red, &s_flag);
+}
+
+// Batched slice guard: block b is slice b - slice_begin of the item whose slices contain it.
+__global__ void slice_guard_batch_kernel(const BatchItem32* __restrict__ items, int n_items,
+                                         unsigned int* __restrict__ flag_count, unsigned int* __restrict__ flag_list) {
+    __shared__ double red[4 * 32];
+    __shared__ int s_flag;
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].slice_begin <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const BatchItem32& it = items[lo];
+    if (std::isinf(it.slice_tol) && it.slice_tol > 0) return;
+    slice_guard_body(it.part, it.scale, (int64_t)blockIdx.x - it.slice_begin, it.g.V3, Momentum(), it.slice_tol,
+                     it.unit_begin, flag_count, flag_list, red, &s_flag);
+}
+
+// Cluster launch of kern with as many clusters as can be resident at once (at most
+// `want` clusters).
+template <class K, class... Args>
+cudaError_t launch_clusters(K kern, int cs, int walkers, int smem, int64_t want, int max_grid, cudaStream_t s,
+                            Args... args) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(d.walkers * kWalker);
-    cfg.dynamicSmemBytes = d.smem_bytes;
+    cfg.blockDim = dim3(walkers * kWalker);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = d.cs;
+    at[0].val.clusterDim.x = cs;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    // as many clusters as can be resident at once (at most one per site)
-    int clusters = max_grid / d.cs;
-    if (d.cs > 1) {
-        cfg.gridDim = dim3(d.cs * clusters);
+    int clusters = max_grid / cs;
+    if (cs > 1) {
+        cfg.gridDim = dim3(cs * clusters);
         int active = 0;
         e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
         if (e != cudaSuccess) return e;
         if (active < 1) return cudaErrorInvalidConfiguration;
         clusters = std::min(clusters, active);
     }
-    clusters = (int)std::max<int64_t>(1, std::min<int64_t>(clusters, g.n_sites()));
-    cfg.gridDim = dim3(d.cs * clusters);
-    e = cudaLaunchKernelEx(&cfg, kern, d, U, D, g, part, (float2*)bslots, flag_count, flag_list, site_guard,
-                           scale_out);
+    clusters = (int)std::max<int64_t>(1, std::min<int64_t>(clusters, want));
+    cfg.gridDim = dim3(cs * clusters);
+    e = cudaLaunchKernelEx(&cfg, kern, args...);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+template <bool REAL, int NJ>
+cudaError_t launch_t(const Eg32Dev& d, const double* U, const double* D, Geometry g, d4* part, int max_grid,
+                     void* bslots, unsigned int* flag_count, unsigned int* flag_list, float site_guard,
+                     double* scale_out, cudaStream_t s) {
+    return launch_clusters(egraph32_kernel<REAL, NJ>, d.cs, d.walkers, d.smem_bytes, g.n_sites(), max_grid, s, d, U,
+                           D, g, part, (float2*)bslots, flag_count, flag_list, site_guard, scale_out);
+}
+
+template <bool REAL, int NJ>
+cudaError_t launch_batch_t(const BatchItem32* items, int n_items, int64_t n_units, int cs, int walkers, int smem,
+                           int max_grid, void* bslots, int64_t bslot_values, unsigned int* flag_count,
+                           unsigned int* flag_list, cudaStream_t s) {
+    return launch_clusters(egraph32_batch_kernel<REAL, NJ>, cs, walkers, smem, n_units, max_grid, s, items, n_items,
+                           n_units, (float2*)bslots, bslot_values, flag_count, flag_list);
 }
 
 }  // namespace
@@ -581,6 +714,25 @@ cudaError_t launch_egraph32(const Eg32Dev& d, const double* U, const double* D, 
     slice_guard_kernel<<<(unsigned)((int64_t)g.n_sets * g.T), 256, 0, s>>>(part, scale, g.V3, mom, slice_tol,
                                                                           flag_count, flag_list);
     ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_egraph32_batch(const BatchItem32* items, int n_items, int64_t n_units, int64_t n_slices, bool real,
+                                  int nj, int cs, int walkers, int smem, int max_grid, void* bslots,
+                                  int64_t bslot_values, unsigned int* flag_count, unsigned int* flag_list,
+                                  cudaStream_t s, int64_t* launches) {
+    if (n_units == 0) return cudaSuccess;
+    cudaError_t e;
+#define MBC_E32B_ARGS items, n_items, n_units, cs, walkers, smem, max_grid, bslots, bslot_values, flag_count, flag_list, s
+    if (real) e = nj <= 2 ? launch_batch_t<true, 2>(MBC_E32B_ARGS) : launch_batch_t<true, 4>(MBC_E32B_ARGS);
+    else e = nj <= 2 ? launch_batch_t<false, 2>(MBC_E32B_ARGS) : launch_batch_t<false, 4>(MBC_E32B_ARGS);
+#undef MBC_E32B_ARGS
+    if (e != cudaSuccess) return e;
+    ++*launches;
+    if (n_slices > 0) {
+        slice_guard_batch_kernel<<<(unsigned)n_slices, 256, 0, s>>>(items, n_items, flag_count, flag_list);
+        ++*launches;
+    }
     return cudaGetLastError();
 }
 
