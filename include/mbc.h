@@ -214,6 +214,8 @@ typedef struct {
     int n_sets, T;
     int64_t V3;
     void* C;                    /* device complex double [n_sets][T] */
+    void* site_out;             /* optional device complex double [n_sets][T][V3]: per-site
+                                   values (as mbc_correlator's site_out), or NULL */
 } mbc_work;
 mbc_status mbc_batch_reserve(mbc_ctx* ctx, const mbc_work* items, int n_items);
 mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_stream stream);
@@ -249,6 +251,31 @@ mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_strea
 mbc_status mbc_plan_set_guard(mbc_plan* plan, double site_threshold, double slice_tolerance);
 mbc_status mbc_plan_get_guard(const mbc_plan* plan, double* site_threshold, double* slice_tolerance);
 mbc_status mbc_fp32_recomputed(mbc_ctx* ctx, int64_t* n_sites);
+
+/* ------------------------------------------------------------------------------------
+ * Tensor e-graph (Sec. 5) of a tensor-network expression: the e-graph (U, M, H) of the
+ * expression's splits E -> sigma -> E1 E2 under the two restrictions of Sec. 5 (each part
+ * contracts an index internally; one part holds a tensor whose indices are all contracted
+ * in E), saturated up to node_limit e-nodes, extracted by the objective of Sec. 5 (the
+ * children's excess parents from distinct e-classes times their flops, ties to the
+ * smaller cost).  Canonical forms rename summed labels s0, s1, ... and open labels o0,
+ * o1, ... over every factor order and every slot order of the antisymmetric tensors.
+ *
+ * expression: "name(i,j,k) name(l,m) ..." (host string; a label used twice is summed, none
+ * more than twice; 1 to 8 tensors); antisymmetric: names of antisymmetric tensors,
+ * space separated (or NULL); dim: index range for the flop counts.  plan (host buffer of
+ * plan_len bytes, or NULL to query *plan_needed) receives the extracted plan as text: a
+ * first line "root <id> sign <+1|-1>" (the expression equals that sign times the root
+ * class's canonical form), then one line per e-class reached from the root:
+ *     class <id> <canonical form> cost <flops> : leaf
+ *     class <id> <canonical form> cost <flops> : prod <id1> [labels] <id2> [labels] sign <+1|-1>
+ * (labels: the class's canonical labels of the two children's open slots; sign: the
+ * relative sign of the children's canonicalisations).  *n_classes, *n_enodes: the
+ * saturated e-graph's size.  Host-only; works on a device -1 context.
+ * ---------------------------------------------------------------------------------- */
+mbc_status mbc_tensor_egraph(mbc_ctx* ctx, const char* expression, const char* antisymmetric, int64_t node_limit,
+                             int dim, char* plan, int64_t plan_len, int64_t* plan_needed, int64_t* n_classes,
+                             int64_t* n_enodes);
 
 /* ------------------------------------------------------------------------------------
  * Launch schedule and autotuning.  A schedule is (threads per block, blocks per SM,

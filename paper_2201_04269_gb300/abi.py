@@ -63,7 +63,7 @@ class mbc_schedule(ctypes.Structure):
 
 class mbc_work(ctypes.Structure):
     _fields_ = [("plan", c_vp), ("U", c_vp), ("D", c_vp), ("n_sets", ctypes.c_int), ("T", ctypes.c_int),
-                ("V3", ctypes.c_int64), ("C", c_vp)]
+                ("V3", ctypes.c_int64), ("C", c_vp), ("site_out", c_vp)]
 
 
 class mbc_block_plan_info(ctypes.Structure):
@@ -109,6 +109,8 @@ SIGNATURES = [
     ("mbc_plan_set_guard", ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double]),
     ("mbc_plan_get_guard", ctypes.c_int, [c_vp, c_dp, c_dp]),
     ("mbc_fp32_recomputed", ctypes.c_int, [c_vp, c_i64p]),
+    ("mbc_tensor_egraph", ctypes.c_int, [c_vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.c_char_p, ctypes.c_int64, c_i64p, c_i64p, c_i64p]),
     ("mbc_correlator_noalloc", ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, c_vp, c_vp]),
     ("mbc_hadron_blocks", ctypes.c_int, [c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int64, c_vp, c_vp]),
     ("mbc_hadron_blocks_projected", ctypes.c_int, [c_vp, ctypes.c_int, c_vp, c_vp, ctypes.c_int, ctypes.c_int,
@@ -321,6 +323,7 @@ def _works(items):
         arr[i].plan = it["plan"]
         arr[i].U, arr[i].D, arr[i].C = dptr(it["U"]), dptr(it["D"]), dptr(it["C"])
         arr[i].n_sets, arr[i].T, arr[i].V3 = it["n_sets"], it["T"], it["V3"]
+        arr[i].site_out = dptr(it.get("site_out"))
     return arr
 
 
@@ -363,6 +366,19 @@ def mbc_fp32_recomputed(ctx):
     n = ctypes.c_int64()
     check(load().mbc_fp32_recomputed(ctx, ctypes.byref(n)), ctx)
     return int(n.value)
+
+
+def mbc_tensor_egraph(ctx, expression, antisymmetric="eps", node_limit=100000, dim=3):
+    """Extracted plan (text lines) and (classes, e-nodes) of a tensor expression's e-graph."""
+    need, nc, nn = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib = load()
+    e, a = expression.encode(), (antisymmetric or "").encode()
+    check(lib.mbc_tensor_egraph(ctx, e, a, node_limit, dim, None, 0, ctypes.byref(need), ctypes.byref(nc),
+                                ctypes.byref(nn)), ctx)
+    buf = ctypes.create_string_buffer(need.value)
+    check(lib.mbc_tensor_egraph(ctx, e, a, node_limit, dim, buf, need.value, ctypes.byref(need), ctypes.byref(nc),
+                                ctypes.byref(nn)), ctx)
+    return buf.value.decode().splitlines(), (nc.value, nn.value)
 
 
 # ------------------------------------------------------------------- hadron blocks

@@ -13,6 +13,8 @@
 #include "device.cuh"
 #include "plan.hpp"
 #include "walk.hpp"
+#include "tegraph.hpp"
+#include "checks.cuh"
 #include "noalloc.hpp"
 #include "ctx.hpp"
 
@@ -50,6 +52,28 @@ mbc_status fail(mbc_ctx* c, mbc_status s, const std::string& m) {
 
 mbc_status cuda_fail(mbc_ctx* c, cudaError_t e, const char* what) {
     return fail(c, MBC_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Bounds-checking build: synchronise and turn a recorded device check into an error
+// (normal build: nothing).
+mbc_status post_checks(mbc_ctx* c, const char* what) {
+#ifdef MBC_DEVICE_CHECKS
+    CheckRecord r1, r2;
+    cudaError_t e = egraph32_checks(&r1);
+    if (e == cudaSuccess) e = egraph_checks(&r2);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    for (const CheckRecord* r : {&r1, &r2})
+        if (r->count > 0) {
+            char buf[256];
+            snprintf(buf, sizeof buf, "%s: device check %d failed %d time(s): value %lld, bound %lld", what, r->code,
+                     r->count, r->value, r->bound);
+            return fail(c, MBC_CUDA, buf);
+        }
+#else
+    (void)c;
+    (void)what;
+#endif
+    return MBC_OK;
 }
 
 bool capturing(cudaStream_t s) {
@@ -253,9 +277,11 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
             }
             soff.push_back((int32_t)rec);
             sw.push_back(width);
+            // the complex form always (a batched launch with complex-weight items uses it
+            // for every item), the real forms when the weights allow
             if (small) s1.resize(rec + (size_t)width * 32, 0u);
-            else if (real) sr.resize(rec + (size_t)width * 32, int2{0, 0});
-            else sc.resize(rec + (size_t)width * 32, int4{0, 0, 0, 0});
+            if (real) sr.resize(rec + (size_t)width * 32, int2{0, 0});
+            sc.resize(rec + (size_t)width * 32, int4{0, 0, 0, 0});
             for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
                 const int it = (sl * 32 + l) * nj + j;
                 for (int k = 0; k < e.g_off[it + 1] - e.g_off[it]; ++k) {
@@ -265,8 +291,8 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
                     std::memcpy(&br, &wr, 4);
                     std::memcpy(&bi, &wi, 4);
                     if (small) s1[rec + (size_t)k * 32 + l] = (uint32_t)a | ((uint32_t)br & 0xFFFF0000u);
-                    else if (real) sr[rec + (size_t)k * 32 + l] = int2{a, br};
-                    else sc[rec + (size_t)k * 32 + l] = int4{a, br, bi, 0};
+                    if (real) sr[rec + (size_t)k * 32 + l] = int2{a, br};
+                    sc[rec + (size_t)k * 32 + l] = int4{a, br, bi, 0};
                 }
             }
             rec += (size_t)width * 32;
@@ -291,9 +317,9 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
                 std::memcpy(&bi, &ci, 4);
                 const int x = (e.pair_b[q] * nrb) * 4 + j;      // B-table offset of column C_b, free index
                 if (real) t2.push_back(int2{x, br});
-                else t4.push_back(int4{x, br, bi, 0});
+                t4.push_back(int4{x, br, bi, 0});
             }
-        toff.push_back((int32_t)(real ? t2.size() : t4.size()));
+        toff.push_back((int32_t)t4.size());
     }
     o.term_off = b.add(toff);
     o.term2 = b.add(t2);
@@ -317,6 +343,13 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
     v.leafbuf_vals = LB * leaf_size;
     v.pk_words = pk_words;
     v.smem_bytes = f32_smem(W, LB, pk_words, stack_vals, leaf_size);
+    v.n_cols_a = (int)e.A.cols.size();
+    v.n_terms = (int64_t)t4.size();
+    v.n_sell = (int64_t)sc.size();
+    for (int f = 0; f < 2; ++f) {
+        wd[f]->n_steps = (int)wk[f].steps.size();
+        wd[f]->n_leaves = (int)wk[f].leaves.size();
+    }
     o.used = true;
     return "";
 }
@@ -674,7 +707,7 @@ mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int
                                 &c->launches);
         if (e == cudaSuccess)
             e = launch_egraph_list(P->ed, u, d, parts, P->sched_df.threads, grid_df, cnt + 2, c->scratch.p,
-                                   (const unsigned int*)c->flags.p, cnt + 1, s, &c->launches);
+                                   (const unsigned int*)c->flags.p, cnt + 1, n_sites, s, &c->launches);
     } else {
         const int grid = (int)std::min<int64_t>(n_sites, (int64_t)c->sms * P->sched.blocks_per_sm);
         st = ensure(c, c->scratch, egraph_kslot_bytes(P->ed) * (size_t)grid, s);
@@ -683,6 +716,8 @@ mbc_status run(mbc_plan* P, const void* U, const void* D, int n_sets, int T, int
                           c->scratch.p, s, &c->launches);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    st = post_checks(c, "kernel");
+    if (st != MBC_OK) return st;
     e = launch_reduce(parts, g, scale, (double2*)C, (double2*)site_out, (d4*)c->site_tmp.p, s, &c->launches, mom);
     if (e != cudaSuccess) return cuda_fail(c, e, "reduction launch");
     return MBC_OK;
@@ -754,7 +789,7 @@ void mbc_destroy(mbc_ctx* c) {
     destroy_block_plans(c);
     Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
                    &c->batch_items, &c->batch_parts, &c->batch_k, &c->blk_part, &c->blk_F, &c->blk_tree,
-                   &c->bslot, &c->flags, &c->gscale, &c->batch32_items};
+                   &c->bslot, &c->flags, &c->gscale, &c->batch32_items, &c->batch32_scale};
     for (Buf* b : bufs) if (b->p) cudaFree(b->p);
     delete c;
 }
@@ -1010,6 +1045,18 @@ bool same_items(const std::vector<mbc_work>& a, const mbc_work* b, int n) {
     return true;
 }
 
+// The FP32 item table holds each plan's guard settings as they were at mbc_batch_reserve;
+// true when mbc_plan_set_guard changed one since.
+bool guards_changed(const mbc_ctx* c, const mbc_work* items) {
+    for (size_t k = 0; k < c->batch32_host.size(); ++k) {
+        const mbc_work& w = items[c->batch32_src[k]];
+        const float g = w.site_out ? w.plan->e32.guard : INFINITY;
+        const BatchItem32& b = c->batch32_host[k];
+        if (!(b.site_guard == g) || !(b.slice_tol == w.plan->slice_tol)) return true;
+    }
+    return false;
+}
+
 mbc_status check_items(mbc_ctx* c, const mbc_work* items, int n_items) {
     if (n_items < 0 || (n_items && !items)) return fail(c, MBC_INVALID_ARG, "bad items");
     if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
@@ -1042,6 +1089,13 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
         const int pr = items[i].plan->hp.prec == MBC_PREC_FP64 ? 0 : 1;
         smem[pr] = std::max(smem[pr], egraph_smem_bytes(items[i].plan->ed, pr));
     }
+    int64_t tmp_sites = 0;               // items returning per-site values share site_tmp
+    for (int i = 0; i < n_items; ++i)
+        if (items[i].site_out) tmp_sites = std::max<int64_t>(tmp_sites, (int64_t)items[i].n_sets * items[i].T * items[i].V3);
+    if (tmp_sites) {
+        st = ensure(c, c->site_tmp, sizeof(d4) * (size_t)tmp_sites, nullptr);
+        if (st != MBC_OK) return st;
+    }
     const size_t max_smem = std::max(smem[0], smem[1]);
     const int by_smem = (int)(225 * 1024 / (max_smem + 3 * 1024));
     const int bps = std::max(1, std::min(by_smem, 2048 / 384));
@@ -1063,7 +1117,8 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
             b.D = (const double*)items[i].D;
             b.part = (d4*)c->batch_parts.p + part_off[i];
             b.unit_begin = units;
-            units += (int64_t)items[i].n_sets * items[i].T * items[i].V3;
+            b.n_sites = (int64_t)items[i].n_sets * items[i].T * items[i].V3;
+            units += b.n_sites;
             c->batch_host[pr].push_back(b);
         }
         c->batch_units[pr] = units;
@@ -1078,6 +1133,7 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
     // FP32 items: one cluster launch over their (item, site) units with their FP32 views,
     // and their double-float views (same unit numbering) for the recompute
     c->batch32_host.clear();
+    c->batch32_src.clear();
     c->batch32_df_host.clear();
     c->batch32_units = 0;
     c->batch32_slices = 0;
@@ -1088,9 +1144,10 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
         const mbc_plan* P = items[i].plan;
         if (P->hp.prec != MBC_PREC_FP32 || P->hp.terms.empty()) continue;
         const Eg32Dev& d = P->e32;
-        if (cs32 == 0) { cs32 = d.cs; w32 = d.walkers; }
-        if (d.cs != cs32 || d.walkers != w32)
-            return fail(c, MBC_UNSUPPORTED, "batched MBC_PREC_FP32 items must share the cluster size and walker count");
+        if (w32 == 0) w32 = d.walkers;
+        cs32 = std::max(cs32, d.cs);                 // items of smaller clusters leave blocks idle
+        if (d.walkers != w32)
+            return fail(c, MBC_UNSUPPORTED, "batched MBC_PREC_FP32 items must share the walker count");
         smem32 = std::max(smem32, d.smem_bytes);
         nj32 = std::max(nj32, d.n_j);
         real32 = real32 && d.real_w;
@@ -1105,15 +1162,18 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
         b.g = Geometry{items[i].n_sets, items[i].T, items[i].V3};
         b.unit_begin = units32;
         b.slice_begin = slices32;
-        b.site_guard = INFINITY;                     // C only: the slice guard protects it
+        // the per-site guard protects per-site values, when the item returns them
+        b.site_guard = items[i].site_out ? (float)P->e32.guard : INFINITY;
         b.slice_tol = P->slice_tol;
         c->batch32_host.push_back(b);
+        c->batch32_src.push_back(i);
         BatchItem bd;
         bd.d = P->ed;
         bd.U = b.U;
         bd.D = b.D;
         bd.part = b.part;
         bd.unit_begin = units32;
+        bd.n_sites = ns;
         c->batch32_df_host.push_back(bd);
         units32 += ns;
         slices32 += (int64_t)items[i].n_sets * items[i].T;
@@ -1122,11 +1182,11 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
         const int clusters = c->sms / cs32;
         st = ensure(c, c->bslot, sizeof(float2) * (size_t)bvals * clusters, nullptr);
         if (st == MBC_OK) st = ensure(c, c->flags, sizeof(unsigned int) * (size_t)units32, nullptr);
-        if (st == MBC_OK) st = ensure(c, c->gscale, sizeof(double) * (size_t)units32, nullptr);
+        if (st == MBC_OK) st = ensure(c, c->batch32_scale, sizeof(double) * (size_t)units32, nullptr);
         if (st == MBC_OK) st = ensure(c, c->batch32_items, (sizeof(BatchItem32) + sizeof(BatchItem)) *
                                                                c->batch32_host.size(), nullptr);
         if (st != MBC_OK) return st;
-        for (auto& b : c->batch32_host) b.scale = (double*)c->gscale.p + b.unit_begin;
+        for (auto& b : c->batch32_host) b.scale = (double*)c->batch32_scale.p + b.unit_begin;
         const size_t n32 = c->batch32_host.size();
         cudaError_t e = cudaMemcpy(c->batch32_items.p, c->batch32_host.data(), sizeof(BatchItem32) * n32,
                                    cudaMemcpyHostToDevice);
@@ -1170,9 +1230,10 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
     mbc_status st = check_items(c, items, n_items);
     if (st != MBC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!same_items(c->batch_reserved, items, n_items)) {
+    if (!same_items(c->batch_reserved, items, n_items) || guards_changed(c, items)) {
         if (capturing(s))
-            return fail(c, MBC_OOM, "mbc_batch inside a stream capture needs mbc_batch_reserve with the same items first");
+            return fail(c, MBC_OOM, "mbc_batch inside a stream capture needs mbc_batch_reserve with the same items "
+                                    "(and guard settings) first");
         st = mbc_batch_reserve(c, items, n_items);
         if (st != MBC_OK) return st;
     }
@@ -1202,10 +1263,13 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
                                       c->bslot.p, c->batch32_bvals, cnt + 1, (unsigned int*)c->flags.p, s,
                                       &c->launches);
         if (e == cudaSuccess)
-            e = launch_egraph_batch_list(tdf, (int)n32, c->batch32_df_threads, c->batch_grid, c->batch32_df_smem,
+            e = launch_egraph_batch_list(tdf, (int)n32, c->batch32_units, c->batch32_df_threads, c->batch_grid,
+                                         c->batch32_df_smem,
                                          cnt + 2, c->batch_k.p, c->batch_kslot, (const unsigned int*)c->flags.p,
                                          cnt + 1, s, &c->launches);
         if (e != cudaSuccess) return cuda_fail(c, e, "batched FP32 launch");
+        st = post_checks(c, "batched FP32 launch");
+        if (st != MBC_OK) return st;
     }
     // site sums per item
     int64_t off = 0;
@@ -1221,7 +1285,9 @@ mbc_status mbc_batch(mbc_ctx* c, const mbc_work* items, int n_items, mbc_stream 
             }
         } else {
             Partials pt{(d4*)c->batch_parts.p + off, 1};
-            cudaError_t e = launch_reduce(pt, g, scale, (double2*)w.C, nullptr, nullptr, s, &c->launches);
+            // (mbc_batch_reserve sized site_tmp for the items that return per-site values)
+            cudaError_t e = launch_reduce(pt, g, scale, (double2*)w.C, (double2*)w.site_out,
+                                          w.site_out ? (d4*)c->site_tmp.p : nullptr, s, &c->launches);
             if (e != cudaSuccess) return cuda_fail(c, e, "reduction launch");
         }
         off += g.n_sites();
@@ -1257,6 +1323,32 @@ mbc_status mbc_fp32_recomputed(mbc_ctx* c, int64_t* n_sites) {
     if (e != cudaSuccess) return cuda_fail(c, e, "reading the recompute count");
     *n_sites = v;
     return MBC_OK;
+}
+
+mbc_status mbc_tensor_egraph(mbc_ctx* c, const char* expression, const char* antisymmetric, int64_t node_limit, int dim,
+                             char* plan, int64_t plan_len, int64_t* plan_needed, int64_t* n_classes, int64_t* n_enodes) {
+    Range range_("mbc_tensor_egraph");
+    if (!c) return MBC_INVALID_ARG;
+    if (!expression || !plan_needed || !n_classes || !n_enodes || dim < 1 || plan_len < 0)
+        return fail(c, MBC_INVALID_ARG, "null argument, dim < 1 or negative buffer length");
+    std::string text;
+    mbc_status st = MBC_OK;
+    try {
+        int64_t nc = 0, nn = 0;
+        std::string err = tensor_egraph(expression, antisymmetric ? antisymmetric : "", node_limit, dim, text, nc, nn);
+        if (!err.empty()) return fail(c, MBC_INVALID_ARG, err);
+        *n_classes = nc;
+        *n_enodes = nn;
+    } catch (const std::bad_alloc&) {
+        return fail(c, MBC_OOM, "host allocation in the tensor e-graph");
+    }
+    *plan_needed = (int64_t)text.size() + 1;
+    if (plan) {
+        if (plan_len < (int64_t)text.size() + 1) return fail(c, MBC_INVALID_ARG, "plan buffer too small");
+        std::memcpy(plan, text.c_str(), text.size() + 1);
+    }
+    c->err.clear();
+    return st;
 }
 
 mbc_status mbc_set_schedule(mbc_plan* P, const mbc_schedule* s) {

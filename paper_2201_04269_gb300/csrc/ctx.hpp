@@ -41,8 +41,9 @@ struct mbc_ctx {
     // error scales
     mbc::Buf bslot, flags, gscale;
     // batched FP32 items: their FP32 and double-float item tables (device) and launch shape
-    mbc::Buf batch32_items;
+    mbc::Buf batch32_items, batch32_scale;
     std::vector<mbc::BatchItem32> batch32_host;
+    std::vector<int> batch32_src;              // the mbc_work index of each FP32 table entry
     std::vector<mbc::BatchItem> batch32_df_host;
     int64_t batch32_units = 0, batch32_slices = 0, batch32_bvals = 0;
     int batch32_cs = 1, batch32_walkers = 1, batch32_smem = 0, batch32_nj = 1, batch32_df_threads = 384;

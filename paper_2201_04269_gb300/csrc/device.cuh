@@ -118,6 +118,7 @@ struct WalkDev {
     const WalkStep* steps;
     const int32_t* step_off;         // [walkers + 1]
     const WalkLeaf* leaves;
+    int n_steps, n_leaves;           // array sizes (bounds-checking build)
 };
 
 // The e-graph plan of the FP32 kernel: the same column trees, G entries and pairs as
@@ -150,6 +151,8 @@ struct Eg32Dev {
     const uint8_t* leaf_jmask;       // per A leaf: bit j set when a pair of the leaf has coef_j != 0
     float guard;                     // a site whose error estimate exceeds this is recomputed
     int smem_bytes;                  // dynamic shared memory of the kernel
+    int n_cols_a;                    // A leaves (column sets)
+    int64_t n_terms, n_sell;         // array sizes (bounds-checking build)
 };
 
 // One item of a batched FP32 launch: the plan's FP32 view, its fields and geometry, where
@@ -176,6 +179,7 @@ struct BatchItem {
     const double* D;
     d4* part;
     int64_t unit_begin;
+    int64_t n_sites;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -202,14 +206,21 @@ cudaError_t launch_egraph32_batch(const BatchItem32* items, int n_items, int64_t
                                   int64_t bslot_values, unsigned int* flag_count, unsigned int* flag_list,
                                   cudaStream_t s, int64_t* launches);
 // The double-float batched kernel over a device list of units (list_n: device count).
-cudaError_t launch_egraph_batch_list(const BatchItem* items, int n_items, int threads, int grid, size_t smem,
-                                     unsigned int* counter, void* kscratch, int64_t kslot_values,
+cudaError_t launch_egraph_batch_list(const BatchItem* items, int n_items, int64_t n_units, int threads, int grid,
+                                     size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values,
                                      const unsigned int* list, const unsigned int* list_n, cudaStream_t s,
                                      int64_t* launches);
 // The double-float e-graph kernel over a device list of sites (list_n: device count).
 cudaError_t launch_egraph_list(const EgraphDev& d, const double* U, const double* D, Partials out, int threads,
                                int grid, unsigned int* counter, void* kscratch, const unsigned int* list,
-                               const unsigned int* list_n, cudaStream_t s, int64_t* launches);
+                               const unsigned int* list_n, int64_t n_sites, cudaStream_t s, int64_t* launches);
+// Bounds-checking build (-DMBC_DEVICE_CHECKS): the first failed device check of the
+// FP32 kernels (egraph32.cu) and of the double-float e-graph kernels (egraph.cu); both
+// synchronise the device and clear the record.  Normal build: always empty.
+struct CheckRecord;
+cudaError_t egraph32_checks(CheckRecord* out);
+cudaError_t egraph_checks(CheckRecord* out);
+
 // Sink momentum of the site sum: p in units of 2 pi / L, site x of a slice at
 // (x mod L, (x / L) mod L, x / L^2); p = 0 is the plain sum.
 struct Momentum {

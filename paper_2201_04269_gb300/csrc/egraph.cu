@@ -23,6 +23,7 @@
 // Mixed precision: the site's 12x12 blocks are scaled by exact powers of two and every
 // product and sum is a double-float operation; the scale is restored in double.
 #include "common.cuh"
+#include "checks.cuh"
 
 namespace mbc {
 
@@ -35,7 +36,11 @@ __device__ __forceinline__ void laplace_k(const MinorDev& m, const uint32_t* pk,
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         uint32_t w[K];
 #pragma unroll
-        for (int i = 0; i < K; ++i) w[i] = pk[i * n + e];
+        for (int i = 0; i < K; ++i) {
+            w[i] = pk[i * n + e];
+            if (MBC_BAD((w[i] >> 16) < 12u && (w[i] & 0xFFFFu) < (uint32_t)m.size[K - 1], 53, w[i], m.size[K - 1]))
+                w[i] = 0;
+        }
         typename P::A acc;
         P::acc_zero(acc);
 #pragma unroll
@@ -164,7 +169,7 @@ template <class P>
 __device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __restrict__ U,
                                             const double* __restrict__ D, int64_t site, d4* part,
                                             typename P::V* __restrict__ kslot, unsigned char* smem_raw, double* red,
-                                            const uint32_t** pk_owner) {
+                                            const uint32_t*& pk_owner) {
     typedef typename P::V V;
     V* sA = reinterpret_cast<V*>(smem_raw);
     V* sB = sA + kBlk;
@@ -175,22 +180,27 @@ __device__ __forceinline__ void egraph_site(const EgraphDev& d, const double* __
     const int n_rb = d.n_rows_b, nj = d.n_j;
     const bool fused = d.compact && nj <= 2;
     V* K = kslot;
-    // packed tables of the two leaf levels: copied to shared memory once per plan when the
-    // plan asks for it (when that costs no resident block), else read through L1
+    // packed tables of the two leaf levels: copied to shared memory when the plan asks for
+    // it (when that costs no resident block), else read through L1.  Where they sit depends
+    // on the plan's stack and G sizes, so a site of another plan (batched items) overwrites
+    // them: pk_owner (the same in every thread) names the plan whose copy is intact, and is
+    // cleared by a site of a plan that does not stage
     const uint32_t* pkA = d.A.pack[nA];
     const uint32_t* pkB = d.B.pack[nB];
     if (d.stage_pk) {
         uint32_t* sa = reinterpret_cast<uint32_t*>(G + (fused ? 0 : nj * n_rb));
         uint32_t* sb = sa + d.A.size[nA] * nA;
-        if (*pk_owner != d.A.pack[nA]) {
+        if (pk_owner != d.A.pack[nA]) {
             __syncthreads();
             for (int i = threadIdx.x; i < d.A.size[nA] * nA; i += blockDim.x) sa[i] = __ldg(d.A.pack[nA] + i);
             for (int i = threadIdx.x; i < d.B.size[nB] * nB; i += blockDim.x) sb[i] = __ldg(d.B.pack[nB] + i);
             __syncthreads();
-            if (threadIdx.x == 0) *pk_owner = d.A.pack[nA];
+            pk_owner = d.A.pack[nA];
         }
         pkA = sa;
         pkB = sb;
+    } else {
+        pk_owner = nullptr;
     }
     // ---- stage the site's blocks (A flavour first)
     const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
@@ -302,12 +312,11 @@ __global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* 
                                                      unsigned int* __restrict__ counter,
                                                      typename P::V* __restrict__ kscratch,
                                                      const unsigned int* __restrict__ list,
-                                                     const unsigned int* __restrict__ list_n) {
+                                                     const unsigned int* __restrict__ list_n, int64_t n_sites_list) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * 32];
     __shared__ unsigned int s_unit;
-    __shared__ const uint32_t* pk_owner;
-    if (threadIdx.x == 0) pk_owner = nullptr;
+    const uint32_t* pk_owner = nullptr;
     typename P::V* K = kscratch + (size_t)blockIdx.x * d.n_cols_b * d.n_rows_b;      // this block's K slot
     // every site of the geometry, or (list mode) the sites of a device list
     const int64_t n_units = list ? (int64_t)*list_n : g.n_sites();
@@ -317,7 +326,8 @@ __global__ void __launch_bounds__(384) egraph_kernel(EgraphDev d, const double* 
         const int64_t unit = s_unit;
         if (unit >= n_units) break;
         const int64_t site = list ? (int64_t)list[unit] : unit;
-        egraph_site<P>(d, U, D, site, out.part + site, K, smem_raw, red, &pk_owner);
+        if (list && MBC_BAD(site >= 0 && site < n_sites_list, 50, site, n_sites_list)) continue;
+        egraph_site<P>(d, U, D, site, out.part + site, K, smem_raw, red, pk_owner);
     }
 }
 
@@ -331,12 +341,12 @@ __global__ void __launch_bounds__(384, 3) egraph_batch_kernel(const BatchItem* _
                                                            int64_t n_units, unsigned int* __restrict__ counter,
                                                            typename P::V* __restrict__ kscratch, int64_t kslot_values,
                                                            const unsigned int* __restrict__ list,
-                                                           const unsigned int* __restrict__ list_n) {
+                                                           const unsigned int* __restrict__ list_n,
+                                                           int64_t n_units_list) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4 * 32];
     __shared__ unsigned int s_unit;
-    __shared__ const uint32_t* pk_owner;
-    if (threadIdx.x == 0) pk_owner = nullptr;
+    const uint32_t* pk_owner = nullptr;
     typename P::V* K = kscratch + (size_t)blockIdx.x * kslot_values;
     // every unit, or (list mode) the units of a device list
     const int64_t n_work = list ? (int64_t)*list_n : n_units;
@@ -346,6 +356,7 @@ __global__ void __launch_bounds__(384, 3) egraph_batch_kernel(const BatchItem* _
         const int64_t work = s_unit;
         if (work >= n_work) break;
         const int64_t unit = list ? (int64_t)list[work] : work;
+        if (list && MBC_BAD(unit >= 0 && unit < n_units_list, 51, unit, n_units_list)) continue;
         int lo = 0, hi = n_items - 1;
         while (lo < hi) {                  // last item whose first unit is <= unit
             const int mid = (lo + hi + 1) >> 1;
@@ -353,7 +364,8 @@ __global__ void __launch_bounds__(384, 3) egraph_batch_kernel(const BatchItem* _
         }
         const BatchItem& it = items[lo];
         const int64_t site = unit - it.unit_begin;
-        egraph_site<P>(it.d, it.U, it.D, site, it.part + site, K, smem_raw, red, &pk_owner);
+        if (MBC_BAD(site >= 0 && site < it.n_sites, 52, site, it.n_sites)) continue;
+        egraph_site<P>(it.d, it.U, it.D, site, it.part + site, K, smem_raw, red, pk_owner);
     }
 }
 
@@ -373,16 +385,16 @@ cudaError_t launch_egraph_batch(const BatchItem* items, int n_items, int64_t n_u
     if (e != cudaSuccess) return e;
     if (prec == 0)
         egraph_batch_kernel<FP64><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cd*)kscratch, kslot_values,
-                                                              nullptr, nullptr);
+                                                              nullptr, nullptr, 0);
     else
         egraph_batch_kernel<MIXED><<<grid, threads, smem, s>>>(items, n_items, n_units, counter, (cdf*)kscratch,
-                                                               kslot_values, nullptr, nullptr);
+                                                               kslot_values, nullptr, nullptr, 0);
     ++*launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_egraph_batch_list(const BatchItem* items, int n_items, int threads, int grid, size_t smem,
-                                     unsigned int* counter, void* kscratch, int64_t kslot_values,
+cudaError_t launch_egraph_batch_list(const BatchItem* items, int n_items, int64_t n_units, int threads, int grid,
+                                     size_t smem, unsigned int* counter, void* kscratch, int64_t kslot_values,
                                      const unsigned int* list, const unsigned int* list_n, cudaStream_t s,
                                      int64_t* launches) {
     if (n_items == 0) return cudaSuccess;
@@ -392,7 +404,7 @@ cudaError_t launch_egraph_batch_list(const BatchItem* items, int n_items, int th
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     egraph_batch_kernel<MIXED><<<grid, threads, smem, s>>>(items, n_items, 0, counter, (cdf*)kscratch, kslot_values,
-                                                           list, list_n);
+                                                           list, list_n, n_units);
     ++*launches;
     return cudaGetLastError();
 }
@@ -411,16 +423,16 @@ cudaError_t launch_egraph(const EgraphDev& d, int prec, const double* U, const d
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     if (prec == 0)
-        egraph_kernel<FP64><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cd*)kscratch, nullptr, nullptr);
+        egraph_kernel<FP64><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cd*)kscratch, nullptr, nullptr, 0);
     else
-        egraph_kernel<MIXED><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cdf*)kscratch, nullptr, nullptr);
+        egraph_kernel<MIXED><<<grid, threads, smem, s>>>(d, U, D, g, out, counter, (cdf*)kscratch, nullptr, nullptr, 0);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_egraph_list(const EgraphDev& d, const double* U, const double* D, Partials out, int threads,
                                int grid, unsigned int* counter, void* kscratch, const unsigned int* list,
-                               const unsigned int* list_n, cudaStream_t s, int64_t* launches) {
+                               const unsigned int* list_n, int64_t n_sites, cudaStream_t s, int64_t* launches) {
     const size_t smem = egraph_smem_bytes(d, 1);
     cudaError_t e = cudaFuncSetAttribute(egraph_kernel<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -429,9 +441,11 @@ cudaError_t launch_egraph_list(const EgraphDev& d, const double* U, const double
     // the list's length is known on the device only: the full persistent grid is
     // launched and blocks without work exit at once
     egraph_kernel<MIXED><<<grid, threads, smem, s>>>(d, U, D, Geometry{0, 0, 0}, out, counter, (cdf*)kscratch, list,
-                                                     list_n);
+                                                     list_n, n_sites);
     ++*launches;
     return cudaGetLastError();
 }
+
+cudaError_t egraph_checks(CheckRecord* out) { return read_checks(out); }
 
 }  // namespace mbc

@@ -28,6 +28,7 @@
 // exceeds the plan's guard (or is not finite) is appended to a list, and the
 // double-float kernel (egraph.cu) recomputes exactly those sites afterwards.
 #include "common.cuh"
+#include "checks.cuh"
 
 namespace mbc {
 namespace {
@@ -137,7 +138,7 @@ __device__ __forceinline__ void stage_f32(const double* __restrict__ a, const do
 // every row set e of level K (packed words transposed: word i of entry e at [i n + e]).
 template <int K>
 __device__ __forceinline__ void lap_node(const float2* M, const uint32_t* pk, int n, int col, int sign,
-                                         const float2* parent, float2* dest, int wt) {
+                                         const float2* parent, float2* dest, int wt, int n_parent) {
     const float2* mc = M + col;
     const unsigned qm = sign < 0 ? 0x80000000u : 0u;
     for (int e = wt; e < n; e += kWalker) {
@@ -147,6 +148,7 @@ __device__ __forceinline__ void lap_node(const float2* M, const uint32_t* pk, in
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < K; ++i) {
+            if (MBC_BAD((int)(w[i] >> 16) < 12 && (int)(w[i] & 0xFFFFu) < n_parent, 1, w[i], n_parent)) continue;
             const float2 p = flip_bits(parent[w[i] & 0xFFFFu], qm ^ ((i & 1) ? 0x80000000u : 0u));
             acc = cfma(acc, mc[(w[i] >> 16) * kLd], p);
         }
@@ -162,7 +164,8 @@ __device__ __forceinline__ void lap_node(const float2* M, const uint32_t* pk, in
 constexpr int kMaxBatch = kMaxLeafBatch;
 template <int K>
 __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, int n, const WalkLeaf* lv,
-                                           int nleaf, const float2* parent, float2* out, bool to_cols, int wt) {
+                                           int nleaf, const float2* parent, float2* out, bool to_cols, int wt,
+                                           int n_parent, int64_t out_bound) {
     int col[kMaxBatch], obase[kMaxBatch];
     unsigned sm[kMaxBatch];
 #pragma unroll
@@ -175,6 +178,7 @@ __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, 
             col[l] = L.col;
             sm[l] = L.sign < 0 ? 0x80000000u : 0u;
             obase[l] = (to_cols ? L.leaf : l) * n;
+            if (MBC_BAD(L.col < 12 && (int64_t)obase[l] + n <= out_bound, 2, obase[l] + n, out_bound)) nleaf = l;
         }
     }
     for (int e = wt; e < n; e += kWalker) {
@@ -182,7 +186,8 @@ __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, 
         const float2* mr[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            const uint32_t w = pk[i * n + e];
+            uint32_t w = pk[i * n + e];
+            if (MBC_BAD((int)(w >> 16) < 12 && (int)(w & 0xFFFFu) < n_parent, 3, w, n_parent)) w = 0;
             mr[i] = M + (int)(w >> 16) * kLd;
             p[i] = flip_bits(parent[w & 0xFFFFu], (i & 1) ? 0x80000000u : 0u);
         }
@@ -199,26 +204,27 @@ __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, 
 }
 
 __device__ __forceinline__ void lap_node_k(int k, const float2* M, const uint32_t* pk, int n, int col, int sign,
-                                           const float2* parent, float2* dest, int wt) {
+                                           const float2* parent, float2* dest, int wt, int n_parent) {
     switch (k) {
-        case 1: lap_node<1>(M, pk, n, col, sign, parent, dest, wt); break;
-        case 2: lap_node<2>(M, pk, n, col, sign, parent, dest, wt); break;
-        case 3: lap_node<3>(M, pk, n, col, sign, parent, dest, wt); break;
-        case 4: lap_node<4>(M, pk, n, col, sign, parent, dest, wt); break;
-        case 5: lap_node<5>(M, pk, n, col, sign, parent, dest, wt); break;
-        default: lap_node<6>(M, pk, n, col, sign, parent, dest, wt); break;
+        case 1: lap_node<1>(M, pk, n, col, sign, parent, dest, wt, n_parent); break;
+        case 2: lap_node<2>(M, pk, n, col, sign, parent, dest, wt, n_parent); break;
+        case 3: lap_node<3>(M, pk, n, col, sign, parent, dest, wt, n_parent); break;
+        case 4: lap_node<4>(M, pk, n, col, sign, parent, dest, wt, n_parent); break;
+        case 5: lap_node<5>(M, pk, n, col, sign, parent, dest, wt, n_parent); break;
+        default: lap_node<6>(M, pk, n, col, sign, parent, dest, wt, n_parent); break;
     }
 }
 
 __device__ __forceinline__ void lap_leaves_k(int k, const float2* M, const uint32_t* pk, int n, const WalkLeaf* lv,
-                                             int nleaf, const float2* parent, float2* out, bool to_cols, int wt) {
+                                             int nleaf, const float2* parent, float2* out, bool to_cols, int wt,
+                                             int n_parent, int64_t out_bound) {
     switch (k) {
-        case 1: lap_leaves<1>(M, pk, n, lv, nleaf, parent, out, to_cols, wt); break;
-        case 2: lap_leaves<2>(M, pk, n, lv, nleaf, parent, out, to_cols, wt); break;
-        case 3: lap_leaves<3>(M, pk, n, lv, nleaf, parent, out, to_cols, wt); break;
-        case 4: lap_leaves<4>(M, pk, n, lv, nleaf, parent, out, to_cols, wt); break;
-        case 5: lap_leaves<5>(M, pk, n, lv, nleaf, parent, out, to_cols, wt); break;
-        default: lap_leaves<6>(M, pk, n, lv, nleaf, parent, out, to_cols, wt); break;
+        case 1: lap_leaves<1>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
+        case 2: lap_leaves<2>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
+        case 3: lap_leaves<3>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
+        case 4: lap_leaves<4>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
+        case 5: lap_leaves<5>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
+        default: lap_leaves<6>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
     }
 }
 
@@ -254,10 +260,12 @@ __device__ __forceinline__ void leaf_stage_n(const Eg32Dev& d, const WalkLeaf* l
     int jm = 0;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        const int id = lv[l].leaf;
+        int id = lv[l].leaf;
+        if (MBC_BAD(id >= 0 && id < d.n_cols_a, 20, id, d.n_cols_a)) id = 0;
         jm |= __ldg(d.leaf_jmask + id);
         lq0[l] = __ldg(d.term_off + id);
         lnt[l] = __ldg(d.term_off + id + 1) - lq0[l];
+        if (MBC_BAD(lq0[l] >= 0 && lq0[l] + lnt[l] <= d.n_terms, 21, lq0[l] + lnt[l], d.n_terms)) lnt[l] = 0;
     }
     for (int b = wt; b < n_rb; b += kWalker) {
         const int sl = b >> 5, lane = b & 31;
@@ -270,7 +278,9 @@ __device__ __forceinline__ void leaf_stage_n(const Eg32Dev& d, const WalkLeaf* l
         for (int j = 0; j < NJ; ++j) {
             if (!((jm >> j) & 1)) continue;
             const int o = __ldg(d.sell_off + sl * d.n_j + j) + lane;
-            const int wd = __ldg(d.sell_w + sl * d.n_j + j);
+            int wd = __ldg(d.sell_w + sl * d.n_j + j);
+            if (MBC_BAD(o >= 0 && o + (int64_t)(wd > 0 ? wd - 1 : 0) * 32 < d.n_sell, 22, o + (int64_t)wd * 32, d.n_sell))
+                wd = 0;
             for (int k = 0; k < wd; ++k) {
                 int a;
                 float2 w;
@@ -287,6 +297,7 @@ __device__ __forceinline__ void leaf_stage_n(const Eg32Dev& d, const WalkLeaf* l
                     a = rec.x;
                     w = make_float2(__int_as_float(rec.y), __int_as_float(rec.z));
                 }
+                if (MBC_BAD(a >= 0 && a < n_e, 23, a, n_e)) a = 0;
                 const float2* ta = leafbuf + a;
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
@@ -313,7 +324,12 @@ __device__ __forceinline__ void leaf_stage_n(const Eg32Dev& d, const WalkLeaf* l
                     int2 r[4];
                     float2 bv[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) r[u] = q + u < nt ? __ldg(tp + q + u) : make_int2(0, 0);
+                    for (int u = 0; u < 4; ++u) {
+                        r[u] = q + u < nt ? __ldg(tp + q + u) : make_int2(0, 0);
+                        if (MBC_BAD(r[u].x >= 0 && (int64_t)(r[u].x >> 2) + b < (int64_t)d.n_cols_b * n_rb, 24,
+                                    (r[u].x >> 2) + b, (int64_t)d.n_cols_b * n_rb))
+                            r[u] = make_int2(0, 0);
+                    }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) bv[u] = __ldcg(btb + (r[u].x >> 2));
 #pragma unroll
@@ -358,19 +374,28 @@ __device__ __forceinline__ void walk(const Eg32Dev& d, const WalkDev& f, bool is
                                      const uint32_t* spk, float2* stack, float2* leafbuf, float2* bt, CAcc& acc,
                                      float& guard, int gw, int w, int wt) {
     const int n = f.n;
-    const int s0 = __ldg(f.step_off + gw), s1 = __ldg(f.step_off + gw + 1);
+    const int s0 = __ldg(f.step_off + gw);
+    int s1 = __ldg(f.step_off + gw + 1);
+    if (MBC_BAD(s0 >= 0 && s1 <= f.n_steps, 10, s1, f.n_steps)) s1 = s0;
     for (int s = s0; s < s1; ++s) {
-        const WalkStep st = f.steps[s];
+        WalkStep st = f.steps[s];
+        if (MBC_BAD(st.level < n && st.leaf0 >= 0 && st.leaf0 + st.nleaf <= f.n_leaves && st.nleaf <= kMaxBatch, 11,
+                    st.leaf0 + st.nleaf, f.n_leaves)) {
+            st.level = 0;
+            st.nleaf = 0;
+        }
         if (st.level > 0) {
             const int k = st.level;
-            lap_node_k(k, M, spk + f.pk_off[k], f.size[k], st.col, st.sign, stack + f.off[k - 1], stack + f.off[k], wt);
+            lap_node_k(k, M, spk + f.pk_off[k], f.size[k], st.col, st.sign, stack + f.off[k - 1], stack + f.off[k], wt,
+                       f.size[k - 1]);
             walker_sync(w);
         }
         if (st.nleaf > 0) {
             if (st.level == 0) walker_sync(w);     // the previous batch may still be read
             const WalkLeaf* lv = f.leaves + st.leaf0;
             lap_leaves_k(n, M, spk + f.pk_off[n], f.size[n], lv, st.nleaf, stack + f.off[n - 1],
-                         is_a ? leafbuf : bt, !is_a, wt);
+                         is_a ? leafbuf : bt, !is_a, wt, f.size[n - 1],
+                         is_a ? (int64_t)d.leafbuf_vals : (int64_t)d.n_cols_b * d.n_rows_b);
             walker_sync(w);
             if (is_a) leaf_stage<REAL, NJ>(d, lv, st.nleaf, leafbuf, f.size[n], bt, acc, guard, wt);
         }
@@ -436,10 +461,13 @@ __device__ __forceinline__ void site32_stage_plan(const Eg32Dev& d, const Site32
 template <bool REAL, int NJ>
 __device__ __forceinline__ void site32(const Eg32Dev& d, const double* __restrict__ U, const double* __restrict__ D,
                                        int64_t site, int64_t unit, d4* __restrict__ part, double* __restrict__ scale_out,
-                                       float2* __restrict__ bt, const Site32Smem& m, int rank, float site_guard,
-                                       unsigned int* __restrict__ flag_count, unsigned int* __restrict__ flag_list) {
+                                       float2* __restrict__ bt, const Site32Smem& m, int rank, int cs,
+                                       float site_guard, unsigned int* __restrict__ flag_count,
+                                       unsigned int* __restrict__ flag_list, unsigned int flag_cap) {
+    // cs: the launch's cluster size; blocks of rank >= d.cs (a batched item planned for
+    // smaller clusters) take part in the barriers and the exchange only
     const int w = threadIdx.x / kWalker, wt = threadIdx.x % kWalker;
-    const int cs = d.cs;
+    const bool active = rank < d.cs;
     const int gw = rank * d.walkers + w;
     const int nA = d.A.n, nB = d.B.n;
     const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
@@ -451,12 +479,12 @@ __device__ __forceinline__ void site32(const Eg32Dev& d, const double* __restric
     float guard = 0.f;
     if (nB == 0) {
         if (threadIdx.x == 0 && rank == 0) bt[0] = make_float2(1.f, 0.f);
-    } else {
+    } else if (active) {
         walk<REAL, NJ>(d, d.B, false, m.sB, m.spk, m.stack, m.leafbuf, bt, acc, guard, gw, w, wt);
     }
     __syncthreads();                                   // the B table is complete
     if (cs > 1) cluster_sync_all();
-    walk<REAL, NJ>(d, d.A, true, m.sA, m.spk, m.stack, m.leafbuf, bt, acc, guard, gw, w, wt);
+    if (active) walk<REAL, NJ>(d, d.A, true, m.sA, m.spk, m.stack, m.leafbuf, bt, acc, guard, gw, w, wt);
     // site value: compensated block sums of the parts and of |part|^2
     kacc re = {0.0, 0.0}, im = {0.0, 0.0}, gs = {0.0, 0.0};
     block_sum_site(acc, guard, re, im, gs.hi, m.red);
@@ -491,7 +519,10 @@ __device__ __forceinline__ void site32(const Eg32Dev& d, const double* __restric
         // per-site guard (when per-site values are returned); a site it sends to the
         // double-float kernel has no FP32 error left for the slice guard
         const bool flag = !(est <= (double)site_guard) || !isfinite(gsum);
-        if (flag) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)unit;
+        if (flag) {
+            const unsigned k = atomicAdd(flag_count, 1u);
+            if (!MBC_BAD(k < flag_cap, 30, k, flag_cap)) flag_list[k] = (unsigned int)unit;
+        }
         scale_out[site] = flag ? 0.0 : ldexp(gsum, sc);
     }
 }
@@ -503,7 +534,8 @@ __global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const doubl
                                                           d4* __restrict__ part, float2* __restrict__ bslots,
                                                           unsigned int* __restrict__ flag_count,
                                                           unsigned int* __restrict__ flag_list,
-                                                          float site_guard, double* __restrict__ scale_out) {
+                                                          float site_guard, double* __restrict__ scale_out,
+                                                          unsigned int flag_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[5 * 32];
     __shared__ double xpart[5 * 16];      // block 0 of a cluster: the blocks' (re, im, guard) sums
@@ -514,7 +546,8 @@ __global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const doubl
     site32_stage_plan(d, m);
     const int64_t n_units = g.n_sites();
     for (int64_t site = cid; site < n_units; site += ncl)
-        site32<REAL, NJ>(d, U, D, site, site, part, scale_out, bt, m, rank, site_guard, flag_count, flag_list);
+        site32<REAL, NJ>(d, U, D, site, site, part, scale_out, bt, m, rank, d.cs, site_guard, flag_count, flag_list,
+                         flag_cap);
 }
 
 // Several (plan, fields) items in one launch: units (item, site) numbered item by item,
@@ -523,7 +556,7 @@ __global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const doubl
 // plan view to shared memory and stages its packed words when the item changes.
 template <bool REAL, int NJ>
 __global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem32* __restrict__ items, int n_items,
-                                                                int64_t n_units, float2* __restrict__ bslots,
+                                                                int64_t n_units, int cs, float2* __restrict__ bslots,
                                                                 int64_t bslot_values,
                                                                 unsigned int* __restrict__ flag_count,
                                                                 unsigned int* __restrict__ flag_list) {
@@ -531,8 +564,8 @@ __global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem3
     __shared__ double red[5 * 32];
     __shared__ double xpart[5 * 16];
     __shared__ Eg32Dev sd;
+    const unsigned int flag_cap = (unsigned int)n_units;
     __shared__ int s_item;
-    const int cs = items[0].d.cs;
     const int rank = cs > 1 ? cluster_rank() : 0;
     const int64_t cid = blockIdx.x / cs, ncl = gridDim.x / cs;
     float2* bt = bslots + (size_t)cid * bslot_values;
@@ -547,7 +580,9 @@ __global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem3
             s_item = lo;
         }
         __syncthreads();
-        const int it = s_item;
+        int it = s_item;
+        if (MBC_BAD(it >= 0 && it < n_items && unit - items[it].unit_begin < items[it].g.n_sites(), 40, unit, n_items))
+            it = 0;
         if (it != cur) {
             if (threadIdx.x == 0) sd = items[it].d;
             __syncthreads();
@@ -556,8 +591,8 @@ __global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem3
         }
         const BatchItem32& item = items[it];
         const Site32Smem m = site32_smem(sd, smem_raw, red, xpart);
-        site32<REAL, NJ>(sd, item.U, item.D, unit - item.unit_begin, unit, item.part, item.scale, bt, m, rank,
-                         item.site_guard, flag_count, flag_list);
+        site32<REAL, NJ>(sd, item.U, item.D, unit - item.unit_begin, unit, item.part, item.scale, bt, m, rank, cs,
+                         item.site_guard, flag_count, flag_list, flag_cap);
     }
 }
 
@@ -572,7 +607,8 @@ constexpr double kSliceErr = 2.5e-7;
 __device__ __forceinline__ void slice_guard_body(const d4* __restrict__ part, const double* __restrict__ scale,
                                                  int64_t st, int64_t V3, Momentum mom, double tol, int64_t unit0,
                                                  unsigned int* __restrict__ flag_count,
-                                                 unsigned int* __restrict__ flag_list, double* red, int* s_flag) {
+                                                 unsigned int* __restrict__ flag_list, unsigned int flag_cap, double* red,
+                                                 int* s_flag) {
     double re = 0.0, im = 0.0, m = 0.0;
     for (int64_t x = threadIdx.x; x < V3; x += blockDim.x) {
         const d4 v = part[st * V3 + x];
@@ -610,21 +646,25 @@ __device__ __forceinline__ void slice_guard_body(const d4* __restrict__ part, co
     __syncthreads();
     if (*s_flag)
         for (int64_t x = threadIdx.x; x < V3; x += blockDim.x)
-            if (scale[st * V3 + x] > 0.0) flag_list[atomicAdd(flag_count, 1u)] = (unsigned int)(unit0 + st * V3 + x);
+            if (scale[st * V3 + x] > 0.0) {
+                const unsigned k = atomicAdd(flag_count, 1u);
+                if (!MBC_BAD(k < flag_cap, 31, k, flag_cap)) flag_list[k] = (unsigned int)(unit0 + st * V3 + x);
+            }
     __syncthreads();
 }
 
 __global__ void slice_guard_kernel(const d4* __restrict__ part, const double* __restrict__ scale, int64_t V3,
                                    Momentum mom, double tol, unsigned int* __restrict__ flag_count,
-                                   unsigned int* __restrict__ flag_list) {
+                                   unsigned int* __restrict__ flag_list, unsigned int flag_cap) {
     __shared__ double red[4 * 32];
     __shared__ int s_flag;
-    slice_guard_body(part, scale, blockIdx.x, V3, mom, tol, 0, flag_count, flag_list, red, &s_flag);
+    slice_guard_body(part, scale, blockIdx.x, V3, mom, tol, 0, flag_count, flag_list, flag_cap, red, &s_flag);
 }
 
 // Batched slice guard: block b is slice b - slice_begin of the item whose slices contain it.
 __global__ void slice_guard_batch_kernel(const BatchItem32* __restrict__ items, int n_items,
-                                         unsigned int* __restrict__ flag_count, unsigned int* __restrict__ flag_list) {
+                                         unsigned int* __restrict__ flag_count, unsigned int* __restrict__ flag_list,
+                                         unsigned int flag_cap) {
     __shared__ double red[4 * 32];
     __shared__ int s_flag;
     int lo = 0, hi = n_items - 1;
@@ -635,7 +675,7 @@ __global__ void slice_guard_batch_kernel(const BatchItem32* __restrict__ items, 
     const BatchItem32& it = items[lo];
     if (std::isinf(it.slice_tol) && it.slice_tol > 0) return;
     slice_guard_body(it.part, it.scale, (int64_t)blockIdx.x - it.slice_begin, it.g.V3, Momentum(), it.slice_tol,
-                     it.unit_begin, flag_count, flag_list, red, &s_flag);
+                     it.unit_begin, flag_count, flag_list, flag_cap, red, &s_flag);
 }
 
 // Cluster launch of kern with as many clusters as can be resident at once (at most
@@ -677,7 +717,8 @@ cudaError_t launch_t(const Eg32Dev& d, const double* U, const double* D, Geometr
                      void* bslots, unsigned int* flag_count, unsigned int* flag_list, float site_guard,
                      double* scale_out, cudaStream_t s) {
     return launch_clusters(egraph32_kernel<REAL, NJ>, d.cs, d.walkers, d.smem_bytes, g.n_sites(), max_grid, s, d, U,
-                           D, g, part, (float2*)bslots, flag_count, flag_list, site_guard, scale_out);
+                           D, g, part, (float2*)bslots, flag_count, flag_list, site_guard, scale_out,
+                           (unsigned int)g.n_sites());
 }
 
 template <bool REAL, int NJ>
@@ -685,7 +726,7 @@ cudaError_t launch_batch_t(const BatchItem32* items, int n_items, int64_t n_unit
                            int max_grid, void* bslots, int64_t bslot_values, unsigned int* flag_count,
                            unsigned int* flag_list, cudaStream_t s) {
     return launch_clusters(egraph32_batch_kernel<REAL, NJ>, cs, walkers, smem, n_units, max_grid, s, items, n_items,
-                           n_units, (float2*)bslots, bslot_values, flag_count, flag_list);
+                           n_units, cs, (float2*)bslots, bslot_values, flag_count, flag_list);
 }
 
 }  // namespace
@@ -712,7 +753,8 @@ cudaError_t launch_egraph32(const Eg32Dev& d, const double* U, const double* D, 
     ++*launches;
     if (std::isinf(slice_tol) && slice_tol > 0) return cudaSuccess;      // slice guard off
     slice_guard_kernel<<<(unsigned)((int64_t)g.n_sets * g.T), 256, 0, s>>>(part, scale, g.V3, mom, slice_tol,
-                                                                          flag_count, flag_list);
+                                                                          flag_count, flag_list,
+                                                                          (unsigned int)g.n_sites());
     ++*launches;
     return cudaGetLastError();
 }
@@ -730,10 +772,13 @@ cudaError_t launch_egraph32_batch(const BatchItem32* items, int n_items, int64_t
     if (e != cudaSuccess) return e;
     ++*launches;
     if (n_slices > 0) {
-        slice_guard_batch_kernel<<<(unsigned)n_slices, 256, 0, s>>>(items, n_items, flag_count, flag_list);
+        slice_guard_batch_kernel<<<(unsigned)n_slices, 256, 0, s>>>(items, n_items, flag_count, flag_list,
+                                                                     (unsigned int)n_units);
         ++*launches;
     }
     return cudaGetLastError();
 }
+
+cudaError_t egraph32_checks(CheckRecord* out) { return read_checks(out); }
 
 }  // namespace mbc
