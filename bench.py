@@ -337,6 +337,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mbc", choices=["mbc", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--no-kernel", action="store_true",
+                    help="skip timing the FP32 kernel alone (the roofline then uses the whole step)")
     ap.add_argument("--fp64-slices", type=int, default=6)
     # other workloads and algorithms (the default is the benchmark's headline configuration)
     ap.add_argument("--op", default=OPERATOR)
@@ -345,7 +348,8 @@ def main():
                          "blocks_local = the block form of the local-sink correlator (FP64)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed", "fp64"],
                     help="fp32 = FP32 with error guards (default), mixed = double-float, fp64")
-    ap.add_argument("--autotune", action="store_true", help="tune the plan's schedule before timing")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the plan's default schedule (default: mbc_autotune on two slices first)")
     ap.add_argument("--guard", type=float, default=None, help="FP32 error-estimate threshold (default: the plan's)")
     ap.add_argument("--lattice", default=f"{L}x{T}", help="L x T, e.g. 16x32")
     ap.add_argument("--slices", type=int, default=0, help="time slices evaluated (0 = all)")
@@ -354,7 +358,8 @@ def main():
     ap.add_argument("--seed", type=int, default=SEED)
     ap.add_argument("--kappa", type=float, default=KAPPA)
     ap.add_argument("--noise", type=float, default=None)
-    ap.add_argument("--batched", action="store_true", help="also time the batched form (always on the headline)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched 64-set workload (timed with the headline on one GPU)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -399,6 +404,83 @@ def timed(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
+BATCHED_OPS = ("proton", "dinucleon_I", "dinucleon_II", "he3_I", "he3_II")
+
+
+def run_batched(local, stream, reps=1):
+    """The batched workload: 64 propagator sets (16 configurations x 4 source times; sets
+    0-31 on 16^3 x 32, 32-63 on 24^3 x 48, about 117 GB generated on the GPU) x the five
+    operators of Eq. 2 and the proton, FP32 e-graph plans with their guards, all 320 items
+    in one mbc_batch (one persistent FP32 launch over every (item, site) unit, the slice
+    guard, the double-float recompute, the site sums) captured in a CUDA graph and timed
+    by replaying it.  The vanishing D_II and He-3 II items cost nothing; their sites are
+    reported apart."""
+    import torch
+    import mbc_inputs as mi
+    from paper_2201_04269_gb300 import Context, abi
+    w = mi.WORKLOADS["batched_64"]
+    ctx = Context(local)
+    plans = {op: ctx.plan_operator(op, "egraph", "fp32") for op in BATCHED_OPS}
+    items, keep = [], []
+    st = stream.cuda_stream
+    live = dead = 0
+    for s in range(w["sets"]):
+        Lb, Tb = (w["L"][0], w["T"][0]) if s < w["sets"] // 2 else (w["L"][1], w["T"][1])
+        V3 = Lb ** 3
+        U = torch.empty(1, Tb, V3, 12, 12, dtype=torch.complex128, device="cuda")
+        D = torch.empty_like(U)
+        mi.fill_device(U.data_ptr(), w["seed"] + s, s, 0, V3, list(range(Tb)), w["kappa"], None, st)
+        mi.fill_device(D.data_ptr(), w["seed"] + s, s, 1, V3, list(range(Tb)), w["kappa"], None, st)
+        keep += [U, D]
+        for op in BATCHED_OPS:
+            C = torch.zeros(1, Tb, dtype=torch.complex128, device="cuda")
+            keep.append(C)
+            items.append(dict(plan=plans[op].handle, U=U, D=D, C=C, site_out=None, n_sets=1, T=Tb, V3=V3))
+            if plans[op].info["canonical_terms"]:
+                live += Tb * V3
+            else:
+                dead += Tb * V3
+    field_bytes = sum(k.numel() * 16 for k in keep if k.dim() == 5)
+    abi.mbc_batch_reserve(ctx.handle, items)
+    ctx.batch(items, stream=stream)                   # warm-up (and the recompute count)
+    torch.cuda.synchronize()
+    recomputed = ctx.fp32_recomputed
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=cap):
+        ctx.batch(items, stream=torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    n0 = ctx.launches
+    ctx.batch(items, stream=stream)
+    torch.cuda.synchronize()
+    launches = ctx.launches - n0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    out = {"workload": "batched: 64 propagator sets (16 configurations x 4 source times; 32 on 16^3x32, 32 on "
+                       "24^3x48) x proton, dinucleon I/II, He-3 I/II = 320 items, FP32 e-graph plans with guards, "
+                       "one mbc_batch in a CUDA graph",
+           "value": live / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": reps, "warmup": 2,
+           "contractions_per_step": live, "vanishing_sites_per_step": dead,
+           "fields_gb": field_bytes / 1e9, "kernel_launches_per_step": launches,
+           "recomputed_sites_per_step": recomputed, "recomputed_fraction": recomputed / max(1, live),
+           "clocks": clk.summary()}
+    del g
+    for p in plans.values():
+        p.destroy()
+    ctx.close()
+    del keep
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_local(args, rank, world, local):
     """The local-sink correlator (e-graph, tree or direct plan) on the GPU."""
     import torch
@@ -427,8 +509,13 @@ def run_local(args, rank, world, local):
                 and args.slices <= 0 and args.sites <= 0 and args.sets == 1 and args.noise is None
                 and args.guard is None)
     tuned = None
-    if args.autotune and args.algo == "egraph" and not fp32:
-        tuned = plan.autotune(U, D, min(n_sites, 27648), stream=stream)
+    if not args.no_autotune and args.algo == "egraph":
+        from paper_2201_04269_gb300 import abi
+        default_schedule = abi.mbc_get_schedule(plan.handle)
+        t0 = time.perf_counter()
+        tuned = {"default": default_schedule,
+                 "tuned": plan.autotune(U, D, min(n_sites, 2 * n_v), stream=stream),
+                 "tuning_sites": min(n_sites, 2 * n_v), "tuning_s": round(time.perf_counter() - t0, 2)}
 
     def step():
         plan.correlator(U, D, C, stream=stream)
@@ -463,11 +550,14 @@ def run_local(args, rank, world, local):
     # guard), so that the step is the FP32 kernel and the site sum
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if fp32:
+    if fp32 and not args.no_kernel:
         plan.set_guard(float("inf"), float("inf"))
         ms_kernel = timed(step, max(1, min(args.steps, 3)), stream)
         plan.set_guard(*guards)
         kname = "egraph32_kernel"
+    elif fp32:
+        ms_kernel = ms
+        kname = "egraph32_kernel (whole step: guard, recompute and site sum included)"
     else:
         ms_kernel = ms
         kname = {"egraph": "egraph_kernel", "tree": "minor_table_kernel + tree_walk_kernel",
@@ -513,18 +603,20 @@ def run_local(args, rank, world, local):
             "normwise": float(np.max(np.abs(cm - c64)) / np.max(np.abs(c64)))}
 
     # end to end through the host-buffer entry point (pinned host memory)
-    U_pin = torch.empty(U.shape, dtype=U.dtype).pin_memory()
-    D_pin = torch.empty(D.shape, dtype=D.dtype).pin_memory()
-    U_pin.copy_(U)
-    D_pin.copy_(D)
-    C_pin = torch.zeros(n_sets, n_t, dtype=torch.complex128).pin_memory()
-    plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
-    t0 = time.perf_counter()
-    plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * n_sites / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(U_pin.numel() * 16 * 2),
-           "d2h_bytes_per_step": int(C_pin.numel() * 16)}
-    del U_pin, D_pin
+    e2e = None
+    if not args.no_e2e:
+        U_pin = torch.empty(U.shape, dtype=U.dtype).pin_memory()
+        D_pin = torch.empty(D.shape, dtype=D.dtype).pin_memory()
+        U_pin.copy_(U)
+        D_pin.copy_(D)
+        C_pin = torch.zeros(n_sets, n_t, dtype=torch.complex128).pin_memory()
+        plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
+        t0 = time.perf_counter()
+        plan.correlator_host(U_pin, D_pin, C_pin, stream=stream)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * n_sites / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(U_pin.numel() * 16 * 2),
+               "d2h_bytes_per_step": int(C_pin.numel() * 16)}
+        del U_pin, D_pin
 
     cpu, accuracy = None, None
     if rank == 0 and headline and not args.no_cpu:
@@ -542,6 +634,14 @@ def run_local(args, rank, world, local):
                     "recomputed_with_site_values": site_recomputed,
                     "C_matches_C_only_call": bool(np.allclose(C.cpu().numpy(), C_main, rtol=1e-6, atol=0))}
         del S
+
+    batched = None
+    if headline and world == 1 and not args.no_batched:
+        del U, D
+        torch.cuda.empty_cache()
+        batched = run_batched(local, stream)
+        if "fp64" in compare:
+            batched["vs_fp64_single_plan_he3"] = batched["value"] / compare["fp64"]["value"]
 
     if rank == 0:
         metric = METRIC if headline else f"sink-site contractions/sec ({args.op}, {Lb}^3x{Tb}, {args.algo}, {args.prec})"
@@ -565,7 +665,7 @@ def run_local(args, rank, world, local):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic (GPU-generated seeded recipe)",
                 "config": config, "roofline": roofline, "compare": compare or None, "accuracy": accuracy,
-                "batched": None, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "batched": batched, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.destroy()
     ctx.close()

@@ -280,9 +280,22 @@ mbc_status mbc_tensor_egraph(mbc_ctx* ctx, const char* expression, const char* a
 /* ------------------------------------------------------------------------------------
  * Launch schedule and autotuning.  A schedule is (threads per block, blocks per SM,
  * sites per work unit); mbc_autotune times the candidate schedules of the plan's
- * kernel on the given fields (a few sites per candidate), keeps the fastest in the
- * plan and in the context's cache keyed by (plan signature, device), and reports it.
- * Synchronises the stream.
+ * kernel on the given fields (the plan's current schedule first, then the candidate
+ * grid; every candidate evaluates the n_sites sites as one time slice four times, the
+ * first untimed), keeps the fastest in the plan and in the context's cache keyed by the
+ * plan signature (a plan made later with the same signature starts from it), and reports
+ * it.  Candidates that do not fit or fail to launch are skipped; on an error the plan
+ * keeps its original schedule.  Synchronises the stream.
+ *
+ * For an MBC_PREC_FP32 e-graph plan the schedule is the FP32 kernel's shape: threads =
+ * 128 x walkers (128..768; a walker is a group of 128 threads walking its part of the
+ * column trees), blocks_per_sm = blocks per site (1 or 2: a thread-block cluster whose
+ * blocks share the site's B table), sites_per_unit = A leaves per leaf batch (1..3, 1
+ * when more than two free indices are in use).  Setting a new shape rebuilds the plan's
+ * FP32 arrays on the device (synchronising the device; MBC_UNSUPPORTED when the shape
+ * needs more shared memory than a block has): CUDA graphs that captured calls of the
+ * plan must be captured again, and the context's mbc_batch_reserve is redone by the next
+ * mbc_batch.
  * ---------------------------------------------------------------------------------- */
 typedef struct { int threads; int blocks_per_sm; int sites_per_unit; } mbc_schedule;
 mbc_status mbc_autotune(mbc_plan* plan, const void* U, const void* D, int64_t n_sites, mbc_stream stream,

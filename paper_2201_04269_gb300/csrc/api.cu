@@ -27,6 +27,14 @@ constexpr double kDefaultGuard = 2.0;
 constexpr double kDefaultSliceTol = 1e-6;
 }
 
+namespace mbc {
+// Shape of an MBC_PREC_FP32 plan's kernel: walkers per block (128 threads each), A leaves
+// per leaf batch, blocks per site (a cluster sharing the site's B table); 0 = automatic.
+struct F32Shape {
+    int walkers = 0, leaf_batch = 0, cluster = 0;
+};
+}  // namespace mbc
+
 struct mbc_plan {
     mbc_ctx* ctx = nullptr;
     HostPlan hp;
@@ -36,6 +44,8 @@ struct mbc_plan {
     TreeDev td{};
     EgraphDev ed{};
     Eg32Dev e32{};                // FP32 e-graph view (MBC_PREC_FP32 plans)
+    void* dev32 = nullptr;        // its arrays (walk programs, packed words, G and pair records)
+    mbc::F32Shape f32_shape;      // forced walkers / leaf batch / blocks per site (0: automatic)
     mbc_schedule sched{256, 2, 1};
     mbc_schedule sched_df{384, 1, 1};   // the double-float recompute of flagged sites (MBC_PREC_FP32)
     double guard = kDefaultGuard;        // per-site error-estimate threshold (MBC_PREC_FP32)
@@ -168,7 +178,7 @@ int f32_smem(int W, int LB, int pk_words, int stack_vals, int leaf_size) {
     return 2 * kBlk * 8 + pk_words * 4 + W * (stack_vals + LB * leaf_size) * 8;
 }
 
-std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
+std::string add_f32(const HostPlan& h, const F32Shape& shape, Eg32Dev& v, Blob& b, F32Offsets& o) {
     const EgraphPlan& e = h.eg;
     if (e.n_j < 1 || e.n_j > 4) return "MBC_PREC_FP32 supports at most 4 free indices in use";
     const MinorPlan* mp[2] = {&e.A, &e.B};
@@ -197,13 +207,24 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
     const int nA = e.A.n;
     const int leaf_size = v.A.size[nA];
     const int stack_vals = std::max(stack[0], stack[1]);
+    // (the leaf stage keeps G of every leaf of a batch in registers: one leaf per batch
+    // when more than two free indices are in use)
+    const int max_lb = std::min(e.n_j <= 2 ? 3 : 1, kMaxLeafBatch);
     int W = 0, LB = 0;
+    if (shape.walkers) {
+        if (shape.walkers < 1 || shape.walkers > 6 || shape.leaf_batch < 1 || shape.leaf_batch > max_lb ||
+            shape.cluster < 0 || shape.cluster > 2)
+            return "MBC_PREC_FP32 shape out of range (walkers 1..6, leaf batch 1..3 (1 with more than two free "
+                   "indices), blocks per site 1..2)";
+        if (f32_smem(shape.walkers, shape.leaf_batch, pk_words, stack_vals, leaf_size) > 220 * 1024)
+            return "MBC_PREC_FP32 shape needs more shared memory than a block has";
+        W = shape.walkers;
+        LB = shape.leaf_batch;
+    }
     for (int w : {6, 4, 2, 1}) {
-        // (the leaf stage keeps G of every leaf of a batch in registers: one leaf per batch
-        // when more than two free indices are in use)
-        for (int lb = std::min(e.n_j <= 2 ? 3 : 1, kMaxLeafBatch); lb >= 1 && !W; --lb)
-            if (f32_smem(w, lb, pk_words, stack_vals, leaf_size) <= 220 * 1024) { W = w; LB = lb; }
         if (W) break;
+        for (int lb = max_lb; lb >= 1 && !W; --lb)
+            if (f32_smem(w, lb, pk_words, stack_vals, leaf_size) <= 220 * 1024) { W = w; LB = lb; }
     }
     if (!W) return "MBC_PREC_FP32: the plan's tables do not fit shared memory";
     const int nrb = e.B.n ? (int)e.B.level_rows[e.B.n].size() : 1;
@@ -226,7 +247,7 @@ std::string add_f32(const HostPlan& h, Eg32Dev& v, Blob& b, F32Offsets& o) {
     }
     // blocks per site: two (a cluster sharing one B table) when one table per SM would
     // take more than half of the 129 MB L2, so that the tables in flight stay resident
-    const int cs = (double)ncb * nrb * 8.0 * 152 > 64.0 * (1 << 20) ? 2 : 1;
+    const int cs = shape.cluster ? shape.cluster : (double)ncb * nrb * 8.0 * 152 > 64.0 * (1 << 20) ? 2 : 1;
     Walks wk[2];
     std::string err = build_walks(e.A, cs * W, LB, costA, wk[0]);
     if (err.empty()) err = build_walks(e.B, cs * W, kMaxLeafBatch, costB, wk[1]);
@@ -374,6 +395,65 @@ void bind_f32(Eg32Dev& v, void* dev, const F32Offsets& o, float guard) {
     v.guard = guard;
 }
 
+// The FP32 view of an MBC_PREC_FP32 e-graph plan in its own device allocation (rebuilt
+// alone when the plan's shape changes).  On failure P->dev32 and P->e32 are unchanged.
+mbc_status upload_f32(mbc_plan* P) {
+    const HostPlan& h = P->hp;
+    if (!(h.prec == MBC_PREC_FP32 && h.algo == MBC_ALGO_EGRAPH && !h.terms.empty())) return MBC_OK;
+    Blob b;
+    F32Offsets f32;
+    Eg32Dev v{};
+    std::string msg = add_f32(h, P->f32_shape, v, b, f32);
+    if (!msg.empty()) return fail(P->ctx, MBC_UNSUPPORTED, msg);
+    void* dev = nullptr;
+    cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
+    if (err != cudaSuccess) return fail(P->ctx, MBC_OOM, std::string("cudaMalloc of FP32 plan arrays failed: ") + cudaGetErrorString(err));
+    err = cudaMemcpy(dev, b.host.data(), b.host.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) { cudaFree(dev); return cuda_fail(P->ctx, err, "cudaMemcpy of FP32 plan arrays"); }
+    bind_f32(v, dev, f32, P->guard > 3.0e38 ? INFINITY : (float)std::max(P->guard, -1.0));
+    if (P->dev32) {
+        cudaDeviceSynchronize();        // work queued with the previous arrays
+        cudaFree(P->dev32);
+    }
+    P->dev32 = dev;
+    P->e32 = v;
+    return MBC_OK;
+}
+
+// The schedule of an MBC_PREC_FP32 plan describes its kernel's shape: threads = 128 x
+// walkers, blocks_per_sm = blocks per site (cluster size), sites_per_unit = leaf batch.
+mbc_schedule f32_schedule(const Eg32Dev& v) { return mbc_schedule{128 * std::max(1, v.walkers), std::max(1, v.cs), std::max(1, v.lb)}; }
+
+// Validate and apply a schedule.  For an MBC_PREC_FP32 plan a new shape rebuilds the
+// plan's FP32 arrays (their device addresses change, so a batch reservation of the
+// context is dropped and re-made by the next mbc_batch); on failure nothing changes.
+mbc_status apply_schedule(mbc_plan* P, const mbc_schedule& s) {
+    if (P->hp.prec == MBC_PREC_FP32 && P->hp.algo == MBC_ALGO_EGRAPH) {
+        if (s.threads < 128 || s.threads > 768 || s.threads % 128 || s.blocks_per_sm < 1 || s.blocks_per_sm > 2 ||
+            s.sites_per_unit < 1 || s.sites_per_unit > 3)
+            return fail(P->ctx, MBC_INVALID_ARG, "MBC_PREC_FP32 schedule out of range (threads 128..768 in steps "
+                                                 "of 128, blocks per site 1..2, leaf batch 1..3)");
+        const mbc_schedule cur = P->sched;
+        if (cur.threads == s.threads && cur.blocks_per_sm == s.blocks_per_sm && cur.sites_per_unit == s.sites_per_unit)
+            return MBC_OK;
+        if (P->hp.terms.empty() || !P->dev32) { P->sched = s; return MBC_OK; }
+        const F32Shape old = P->f32_shape;
+        P->f32_shape = F32Shape{s.threads / 128, s.sites_per_unit, s.blocks_per_sm};
+        const mbc_status st = upload_f32(P);
+        if (st != MBC_OK) { P->f32_shape = old; return st; }
+        P->sched = f32_schedule(P->e32);
+        P->ctx->batch_reserved.clear();
+        return MBC_OK;
+    }
+    const int max_threads = P->hp.algo == MBC_ALGO_EGRAPH ? 384 : 256;
+    if (s.threads < 32 || s.threads > max_threads || s.threads % 32 || s.blocks_per_sm < 1 || s.blocks_per_sm > 32 ||
+        s.sites_per_unit < 1)
+        return fail(P->ctx, MBC_INVALID_ARG, "schedule out of range (threads 32..256, or ..384 for the e-graph kernels, "
+                                             "a multiple of 32)");
+    P->sched = s;
+    return MBC_OK;
+}
+
 mbc_status upload(mbc_plan* P) {
     HostPlan& h = P->hp;
     Blob b;
@@ -488,11 +568,6 @@ mbc_status upload(mbc_plan* P) {
             for (int j = 0; j < e.n_j && j < 8; ++j)
                 if (e.pair_coef[(size_t)q * e.n_j + j] != 0.0) jmask[l] |= (uint8_t)(1u << j);
     size_t o_jm = b.add(jmask);
-    F32Offsets f32;
-    if (h.prec == MBC_PREC_FP32 && h.algo == MBC_ALGO_EGRAPH && !h.terms.empty()) {
-        std::string err = add_f32(h, P->e32, b, f32);
-        if (!err.empty()) return fail(P->ctx, MBC_UNSUPPORTED, err);
-    }
 
     void* dev = nullptr;
     cudaError_t err = cudaMalloc(&dev, std::max<size_t>(b.host.size(), 256));
@@ -568,8 +643,7 @@ mbc_status upload(mbc_plan* P) {
     ed.stage_pk = (base + pk16) * 16 <= 200 * 1024 &&
                   (h.prec == MBC_PREC_FP64 || resident(base + pk16) >= resident(base));
     ed.smem_values = base + (ed.stage_pk ? pk16 : 0);
-    if (f32.used) bind_f32(P->e32, dev, f32, (float)P->guard);
-    return MBC_OK;
+    return upload_f32(P);
 }
 
 std::string signature(const HostPlan& h) {
@@ -611,16 +685,19 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
     } catch (const std::bad_alloc&) {
         st = fail(ctx, MBC_OOM, "host allocation while uploading the plan");
     }
-    if (st != MBC_OK) { delete P; return st; }
+    if (st != MBC_OK) {
+        if (P->dev) cudaFree(P->dev);
+        delete P;
+        return st;
+    }
     if (h.algo == MBC_ALGO_EGRAPH && P->ed.smem_values * 16 > 200 * 1024) {
         cudaFree(P->dev);
+        if (P->dev32) cudaFree(P->dev32);
         delete P;
         return fail(ctx, MBC_UNSUPPORTED, "e-graph plan needs more shared memory than a block has");
     }
     P->signature = signature(h);
-    auto it = ctx->tune_cache.find(P->signature);
-    if (it != ctx->tune_cache.end()) P->sched = it->second;
-    else if (h.algo == MBC_ALGO_EGRAPH) {
+    if (h.algo == MBC_ALGO_EGRAPH) {
         // 384 threads (12 warps) per block, or the B row-set count rounded up to whole warps
         // when that lies in 257..384 (one row set per thread in the leaf stage, no idle
         // warp), as many blocks per SM as shared memory and the 2048-thread limit allow
@@ -629,8 +706,11 @@ mbc_status finish_plan(mbc_ctx* ctx, mbc_plan* P, mbc_plan** out) {
         const int by_smem = (int)(225 * 1024 / (P->ed.smem_values * 16 + 3 * 1024));
         P->sched.blocks_per_sm = std::max(1, std::min(by_smem, 2048 / P->sched.threads));
         P->sched_df = P->sched;
-        if (h.prec == MBC_PREC_FP32) P->sched = mbc_schedule{128 * std::max(1, P->e32.walkers), 1, 1};
+        if (h.prec == MBC_PREC_FP32) P->sched = f32_schedule(P->e32);
     }
+    // a schedule tuned earlier for the same plan signature (kept only if it applies)
+    auto it = ctx->tune_cache.find(P->signature);
+    if (it != ctx->tune_cache.end() && apply_schedule(P, it->second) != MBC_OK) ctx->err.clear();
     ctx->plans.push_back(P);
     *out = P;
     ctx->err.clear();
@@ -906,6 +986,7 @@ void mbc_plan_destroy(mbc_plan* P) {
         c->plans.erase(std::remove(c->plans.begin(), c->plans.end(), P), c->plans.end());
     }
     if (P->dev) cudaFree(P->dev);
+    if (P->dev32) cudaFree(P->dev32);
     delete P;
 }
 
@@ -1144,10 +1225,9 @@ mbc_status mbc_batch_reserve(mbc_ctx* c, const mbc_work* items, int n_items) {
         const mbc_plan* P = items[i].plan;
         if (P->hp.prec != MBC_PREC_FP32 || P->hp.terms.empty()) continue;
         const Eg32Dev& d = P->e32;
-        if (w32 == 0) w32 = d.walkers;
-        cs32 = std::max(cs32, d.cs);                 // items of smaller clusters leave blocks idle
-        if (d.walkers != w32)
-            return fail(c, MBC_UNSUPPORTED, "batched MBC_PREC_FP32 items must share the walker count");
+        // items of smaller clusters leave blocks idle, items of fewer walkers leave warps idle
+        w32 = std::max(w32, d.walkers);
+        cs32 = std::max(cs32, d.cs);
         smem32 = std::max(smem32, d.smem_bytes);
         nj32 = std::max(nj32, d.n_j);
         real32 = real32 && d.real_w;
@@ -1353,13 +1433,7 @@ mbc_status mbc_tensor_egraph(mbc_ctx* c, const char* expression, const char* ant
 
 mbc_status mbc_set_schedule(mbc_plan* P, const mbc_schedule* s) {
     if (!P || !s) return MBC_INVALID_ARG;
-    const int max_threads = P->hp.algo == MBC_ALGO_EGRAPH ? 384 : 256;
-    if (s->threads < 32 || s->threads > max_threads || s->threads % 32 || s->blocks_per_sm < 1 || s->blocks_per_sm > 32 ||
-        s->sites_per_unit < 1)
-        return fail(P->ctx, MBC_INVALID_ARG, "schedule out of range (threads 32..256, or ..384 for the e-graph kernels, "
-                                             "a multiple of 32)");
-    P->sched = *s;
-    return MBC_OK;
+    return apply_schedule(P, *s);
 }
 
 mbc_status mbc_get_schedule(const mbc_plan* P, mbc_schedule* s) {
@@ -1376,30 +1450,36 @@ mbc_status mbc_autotune(mbc_plan* P, const void* U, const void* D, int64_t n_sit
     if (c->device < 0) return fail(c, MBC_UNSUPPORTED, "host-only context (device -1) cannot evaluate");
     cudaStream_t s = (cudaStream_t)stream;
     const mbc_schedule orig = P->sched;
-    if (P->hp.prec == MBC_PREC_FP32) {
-        // the FP32 kernel's shape (walkers, leaf batch) is fixed by the plan's shared memory
-        if (best) *best = orig;
-        return MBC_OK;
-    }
+    const bool fp32 = P->hp.prec == MBC_PREC_FP32 && P->hp.algo == MBC_ALGO_EGRAPH;
+    auto same = [](const mbc_schedule& a, const mbc_schedule& b) {
+        return a.threads == b.threads && a.blocks_per_sm == b.blocks_per_sm && a.sites_per_unit == b.sites_per_unit;
+    };
     // candidates: the plan's current (default) schedule first, then the grid of block
-    // sizes x blocks per SM (x sites per unit for the direct sweep)
+    // sizes x blocks per SM (x sites per unit for the direct sweep); for an FP32 plan the
+    // grid of kernel shapes, walkers x blocks per site x leaf batch
     std::vector<mbc_schedule> cands{orig};
-    const int smem = P->ed.smem_values * 16 + 1024;
-    for (int th : {128, 256, 320, 352, 384})
-        for (int bps : {1, 2, 3, 4, 6, 8}) {
-            if (th > 256 && P->hp.algo != MBC_ALGO_EGRAPH) continue;
-            if (th * bps > 2048) continue;
-            if (P->hp.algo == MBC_ALGO_EGRAPH && bps * smem > 220 * 1024) continue;
-            if (P->hp.algo != MBC_ALGO_EGRAPH && bps != 2) continue;
-            for (int spu : {1, 4}) {
-                if (P->hp.algo != MBC_ALGO_DIRECT && spu != 1) continue;
-                const mbc_schedule cs{th, bps, spu};
-                if (cs.threads == orig.threads && cs.blocks_per_sm == orig.blocks_per_sm &&
-                    cs.sites_per_unit == orig.sites_per_unit)
-                    continue;
-                cands.push_back(cs);
+    if (fp32) {
+        for (int w : {3, 4, 5, 6})
+            for (int cs : {1, 2})
+                for (int lb : {1, 2, 3}) {
+                    const mbc_schedule cand{128 * w, cs, lb};
+                    if (!same(cand, orig)) cands.push_back(cand);
+                }
+    } else {
+        const int smem = P->ed.smem_values * 16 + 1024;
+        for (int th : {128, 256, 320, 352, 384})
+            for (int bps : {1, 2, 3, 4, 6, 8}) {
+                if (th > 256 && P->hp.algo != MBC_ALGO_EGRAPH) continue;
+                if (th * bps > 2048) continue;
+                if (P->hp.algo == MBC_ALGO_EGRAPH && bps * smem > 220 * 1024) continue;
+                if (P->hp.algo != MBC_ALGO_EGRAPH && bps != 2) continue;
+                for (int spu : {1, 4}) {
+                    if (P->hp.algo != MBC_ALGO_DIRECT && spu != 1) continue;
+                    const mbc_schedule cand{th, bps, spu};
+                    if (!same(cand, orig)) cands.push_back(cand);
+                }
             }
-        }
+    }
     Buf C;
     cudaError_t e = cudaMalloc(&C.p, sizeof(double2) * (size_t)n_sites);
     if (e != cudaSuccess) return fail(c, MBC_OOM, "autotune output");
@@ -1410,34 +1490,42 @@ mbc_status mbc_autotune(mbc_plan* P, const void* U, const void* D, int64_t n_sit
         cudaFree(C.p);
         return st;
     };
+    // leave the plan with `keep` (its original schedule when tuning fails)
+    auto restore = [&](const mbc_schedule& keep) {
+        const std::string msg = c->err;
+        apply_schedule(P, keep);          // (on failure the plan keeps a shape it ran with)
+        c->err = msg;
+    };
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
-        P->sched = orig;
+        restore(orig);
         return done(fail(c, MBC_CUDA, "autotune events"));
     }
     float best_ms = -1.f;
     mbc_schedule keep = orig;
     for (auto& cand : cands) {
-        P->sched = cand;
-        // warm-up (and pool growth); a candidate that cannot run is skipped
-        mbc_status st = run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);
+        // a candidate that does not apply (shape too large for shared memory) or cannot
+        // run is skipped
+        if (apply_schedule(P, cand) != MBC_OK) continue;
+        mbc_status st = run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);      // warm-up (and pool growth)
         if (st != MBC_OK) {
-            if (st == MBC_CUDA) { P->sched = orig; return done(st); }   // the context may be unusable
+            if (st == MBC_CUDA) { restore(orig); return done(st); }   // the context may be unusable
             continue;
         }
         cudaEventRecord(a, s);
         for (int r = 0; r < 3 && st == MBC_OK; ++r) st = run(P, U, D, 1, 1, n_sites, C.p, nullptr, s);
         cudaEventRecord(b, s);
         e = cudaEventSynchronize(b);
-        if (e != cudaSuccess) { P->sched = orig; return done(cuda_fail(c, e, "autotune timing")); }
+        if (e != cudaSuccess) { restore(orig); return done(cuda_fail(c, e, "autotune timing")); }
         if (st != MBC_OK) continue;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a, b);
         if (best_ms < 0 || ms < best_ms) { best_ms = ms; keep = cand; }
     }
-    P->sched = keep;
+    c->err.clear();
+    restore(keep);
+    keep = P->sched;
     c->tune_cache[P->signature] = keep;
     if (best) *best = keep;
-    c->err.clear();
     return done(MBC_OK);
 }
 

@@ -448,7 +448,7 @@ __device__ __forceinline__ Site32Smem site32_smem(const Eg32Dev& d, unsigned cha
 __device__ __forceinline__ void site32_stage_plan(const Eg32Dev& d, const Site32Smem& m) {
     __syncthreads();
     for (int i = threadIdx.x; i < d.pk_words; i += blockDim.x) m.spk[i] = __ldg(d.pk + i);
-    if (threadIdx.x % kWalker == 0) m.stack[0] = make_float2(1.f, 0.f);
+    if (threadIdx.x % kWalker == 0 && threadIdx.x / kWalker < d.walkers) m.stack[0] = make_float2(1.f, 0.f);
     __syncthreads();
 }
 
@@ -465,9 +465,10 @@ __device__ __forceinline__ void site32(const Eg32Dev& d, const double* __restric
                                        float site_guard, unsigned int* __restrict__ flag_count,
                                        unsigned int* __restrict__ flag_list, unsigned int flag_cap) {
     // cs: the launch's cluster size; blocks of rank >= d.cs (a batched item planned for
-    // smaller clusters) take part in the barriers and the exchange only
+    // smaller clusters) and walkers w >= d.walkers (an item planned for fewer walkers than
+    // the launch's blocks have) take part in the barriers and the exchange only
     const int w = threadIdx.x / kWalker, wt = threadIdx.x % kWalker;
-    const bool active = rank < d.cs;
+    const bool active = rank < d.cs && w < d.walkers;
     const int gw = rank * d.walkers + w;
     const int nA = d.A.n, nB = d.B.n;
     const double* ma = (d.flav_a == 0 ? U : D) + site * 288;
@@ -551,9 +552,11 @@ __global__ void __launch_bounds__(768, 1) egraph32_kernel(Eg32Dev d, const doubl
 }
 
 // Several (plan, fields) items in one launch: units (item, site) numbered item by item,
-// assigned round robin to the grid's clusters.  Every item has this launch's cluster
-// size, walker count, free-index maximum NJ and weight kind.  A block copies the item's
-// plan view to shared memory and stages its packed words when the item changes.
+// assigned round robin to the grid's clusters.  The launch takes the largest cluster size
+// and walker count among the items (an item planned for fewer leaves the extra blocks or
+// warps idle), their largest free-index count NJ, and complex weights if any item has
+// them.  A block copies the item's plan view to shared memory and stages its packed words
+// when the item changes.
 template <bool REAL, int NJ>
 __global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem32* __restrict__ items, int n_items,
                                                                 int64_t n_units, int cs, float2* __restrict__ bslots,

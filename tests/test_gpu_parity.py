@@ -321,6 +321,42 @@ def test_autotune_never_slower_than_default():
     ctx.close()
 
 
+def test_fp32_autotune_shapes():
+    """For an FP32 plan the tuner times kernel shapes (walkers x blocks per site x leaf
+    batch), rebuilding the plan's FP32 arrays per candidate: the shape it keeps is never
+    slower than the default (re-timed, within 10 %), results stay within the FP32 target,
+    an impossible shape is rejected with the plan unchanged, and a plan made later with
+    the same signature starts from the tuned shape."""
+    from paper_2201_04269_gb300 import abi, Context
+    ctx = Context(0)
+    U, D = mi.workload_fields("he3_24x48", L=12, t_list=[2, 20])
+    plan = ctx.plan_operator("he3_II_s", "egraph", "fp32")
+    default = abi.mbc_get_schedule(plan.handle)
+    assert default["threads"] % 128 == 0 and default["blocks_per_sm"] in (1, 2)
+    C1, S1 = run(plan, U[None], D[None])
+    with pytest.raises(abi.MbcError):
+        abi.mbc_set_schedule(plan.handle, 6 * 128, 1, 7)        # leaf batch out of range
+    assert abi.mbc_get_schedule(plan.handle) == default
+    s = plan.autotune(dev(U), dev(D), U.shape[0] * U.shape[1])
+    assert s == abi.mbc_get_schedule(plan.handle)
+    assert s["threads"] % 128 == 0 and 128 <= s["threads"] <= 768 and s["blocks_per_sm"] in (1, 2)
+    C2, S2 = run(plan, U[None], D[None])
+    assert relerr(C2, C1) <= 2 * FP32_C_TOL            # each within the target of the exact C(t)
+    check(S2, S1, "fp32")
+    t_tuned = _time_runs(plan, U, D)
+    abi.mbc_set_schedule(plan.handle, default["threads"], default["blocks_per_sm"], default["sites_per_unit"])
+    assert abi.mbc_get_schedule(plan.handle) == default
+    C3, _ = run(plan, U[None], D[None])
+    assert np.array_equal(C3, C1)
+    t_default = _time_runs(plan, U, D)
+    assert t_tuned <= 1.10 * t_default, (s, default, t_tuned, t_default)
+    p2 = ctx.plan_operator("he3_II_s", "egraph", "fp32")
+    assert abi.mbc_get_schedule(p2.handle) == s
+    p2.destroy()
+    plan.destroy()
+    ctx.close()
+
+
 @pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_random_complex_factored(ctx, algo, prec):
