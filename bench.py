@@ -360,6 +360,8 @@ def main():
     ap.add_argument("--noise", type=float, default=None)
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 64-set workload (timed with the headline on one GPU)")
+    ap.add_argument("--batched-sets", type=int, default=64, help="propagator sets of the batched workload")
+    ap.add_argument("--save-c", default=None, help="write the timed run's C(t) [sets, T] to this .npy file")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -407,14 +409,16 @@ def timed(fn, reps, stream):
 BATCHED_OPS = ("proton", "dinucleon_I", "dinucleon_II", "he3_I", "he3_II")
 
 
-def run_batched(local, stream, reps=1):
+def run_batched(local, stream, n_sets=64):
     """The batched workload: 64 propagator sets (16 configurations x 4 source times; sets
     0-31 on 16^3 x 32, 32-63 on 24^3 x 48, about 117 GB generated on the GPU) x the five
     operators of Eq. 2 and the proton, FP32 e-graph plans with their guards, all 320 items
     in one mbc_batch (one persistent FP32 launch over every (item, site) unit, the slice
     guard, the double-float recompute, the site sums) captured in a CUDA graph and timed
-    by replaying it.  The vanishing D_II and He-3 II items cost nothing; their sites are
-    reported apart."""
+    over one replay (a step takes minutes; the capture itself loads the kernels and the
+    reservation sizes every buffer, so there is no untimed warm-up).  The vanishing D_II
+    and He-3 II items cost nothing; their sites are reported apart.  n_sets < 64 takes the
+    first n_sets / 2 sets of each lattice."""
     import torch
     import mbc_inputs as mi
     from paper_2201_04269_gb300 import Context, abi
@@ -424,8 +428,9 @@ def run_batched(local, stream, reps=1):
     items, keep = [], []
     st = stream.cuda_stream
     live = dead = 0
-    for s in range(w["sets"]):
-        Lb, Tb = (w["L"][0], w["T"][0]) if s < w["sets"] // 2 else (w["L"][1], w["T"][1])
+    half = w["sets"] // 2
+    for s in [k for k in range(w["sets"]) if k % half < n_sets // 2]:
+        Lb, Tb = (w["L"][0], w["T"][0]) if s < half else (w["L"][1], w["T"][1])
         V3 = Lb ** 3
         U = torch.empty(1, Tb, V3, 12, 12, dtype=torch.complex128, device="cuda")
         D = torch.empty_like(U)
@@ -442,32 +447,27 @@ def run_batched(local, stream, reps=1):
                 dead += Tb * V3
     field_bytes = sum(k.numel() * 16 for k in keep if k.dim() == 5)
     abi.mbc_batch_reserve(ctx.handle, items)
-    ctx.batch(items, stream=stream)                   # warm-up (and the recompute count)
     torch.cuda.synchronize()
-    recomputed = ctx.fp32_recomputed
     g = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream()
+    n0 = ctx.launches
     with torch.cuda.graph(g, stream=cap):
         ctx.batch(items, stream=torch.cuda.current_stream())
-    g.replay()
+    launches = ctx.launches - n0                      # the kernels the graph holds
     torch.cuda.synchronize()
-    n0 = ctx.launches
-    ctx.batch(items, stream=stream)
-    torch.cuda.synchronize()
-    launches = ctx.launches - n0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(reps):
-            g.replay()
+        g.replay()
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    out = {"workload": "batched: 64 propagator sets (16 configurations x 4 source times; 32 on 16^3x32, 32 on "
-                       "24^3x48) x proton, dinucleon I/II, He-3 I/II = 320 items, FP32 e-graph plans with guards, "
-                       "one mbc_batch in a CUDA graph",
-           "value": live / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": reps, "warmup": 2,
+    ms = e0.elapsed_time(e1)
+    recomputed = ctx.fp32_recomputed
+    out = {"workload": f"batched: {n_sets} propagator sets ({n_sets // 2} on 16^3x32, {n_sets // 2} on 24^3x48) x "
+                       f"proton, dinucleon I/II, He-3 I/II = {len(items)} items, FP32 e-graph plans with guards, "
+                       "one mbc_batch captured in a CUDA graph",
+           "value": live / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": 1, "warmup": 0,
            "contractions_per_step": live, "vanishing_sites_per_step": dead,
            "fields_gb": field_bytes / 1e9, "kernel_launches_per_step": launches,
            "recomputed_sites_per_step": recomputed, "recomputed_fraction": recomputed / max(1, live),
@@ -543,6 +543,8 @@ def run_local(args, rank, world, local):
         ms = float(t.item())
     clocks = clk.summary()
     C_main = C.cpu().numpy().copy()
+    if args.save_c and rank == 0:
+        np.save(args.save_c, C_main)
     recomputed = ctx.fp32_recomputed if fp32 else 0
     guards = plan.guard if fp32 else None
 
@@ -639,7 +641,7 @@ def run_local(args, rank, world, local):
     if headline and world == 1 and not args.no_batched:
         del U, D
         torch.cuda.empty_cache()
-        batched = run_batched(local, stream)
+        batched = run_batched(local, stream, args.batched_sets)
         if "fp64" in compare:
             batched["vs_fp64_single_plan_he3"] = batched["value"] / compare["fp64"]["value"]
 

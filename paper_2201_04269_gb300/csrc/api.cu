@@ -245,9 +245,11 @@ std::string add_f32(const HostPlan& h, const F32Shape& shape, Eg32Dev& v, Blob& 
         }
         costA[l] = c;
     }
-    // blocks per site: two (a cluster sharing one B table) when one table per SM would
-    // take more than half of the 129 MB L2, so that the tables in flight stay resident
-    const int cs = shape.cluster ? shape.cluster : (double)ncb * nrb * 8.0 * 152 > 64.0 * (1 << 20) ? 2 : 1;
+    // blocks per site: one unless the shape asks for two (a thread-block cluster sharing
+    // one B table, which halves the tables in flight in L2 but adds two cluster barriers
+    // and an exchange per site: measured 5 % slower on 3He_II-s at 24^3 x 48, where one
+    // table per SM, 152 x 0.94 MB, slightly exceeds the L2)
+    const int cs = shape.cluster ? shape.cluster : 1;
     Walks wk[2];
     std::string err = build_walks(e.A, cs * W, LB, costA, wk[0]);
     if (err.empty()) err = build_walks(e.B, cs * W, kMaxLeafBatch, costB, wk[1]);

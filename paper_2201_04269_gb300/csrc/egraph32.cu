@@ -601,11 +601,14 @@ __global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem3
 
 // The slice guard: one block per (set, t).  The FP32 error of C(t) is estimated as
 //   err(t) = kSliceErr * sqrt(sum_x s_x^2),   s_x = sqrt(sum |part|^2) of site x,
-// (the sites' rounding errors add like independent random numbers; kSliceErr is the
-// ratio of a site's FP32 error to s_x, measured about 1e-7 typical and 1.5e-7 rms on the
-// He-3 workloads, taken with margin), and when err(t) > tol |C(t)| every site of the
-// slice that is not recomputed already is appended to the recompute list.  C(t) here
-// is the FP32 estimate with the momentum phase of the site sum.
+// (the sites' rounding errors add like independent random numbers, so the slice's error
+// is close to a complex Gaussian of rms r sqrt(sum_x s_x^2), r the rms ratio of a site's
+// FP32 error to s_x, measured 1.5e-7 on the He-3 workloads; kSliceErr = 1.67 r.  It is an
+// estimate, not a bound: 4e-7 (2.67 r) recomputed three times as many slices of the He-3
+// workload at 24^3 x 48 without changing its largest C(t) error, 8.2e-7), and when
+// err(t) > tol |C(t)| every site of the slice that is not recomputed already is appended
+// to the recompute list.  C(t) here is the FP32 estimate with the momentum phase of the
+// site sum.
 constexpr double kSliceErr = 2.5e-7;
 __device__ __forceinline__ void slice_guard_body(const d4* __restrict__ part, const double* __restrict__ scale,
                                                  int64_t st, int64_t V3, Momentum mom, double tol, int64_t unit0,
