@@ -563,7 +563,8 @@ def test_fp32_sampled_24x48_and_deterministic(ctx):
     ts = rng.integers(0, 48, size=24)
     xs = rng.integers(0, 24 ** 3, size=24)
     ref = oracle_sites("he3_II_s", U[ts, xs], D[ts, xs])
-    check(S1[0][ts, xs], ref, "fp32")
+    e = relerr(S1[0][ts, xs], ref)
+    assert e <= FP32_C_TOL, e            # per-site values (site guard on) at the 1e-6 target
     pdf = ctx.plan_operator("he3_II_s", "egraph", "mixed")
     Cd, _ = run(pdf, U[None], D[None])
     assert relerr(C1, Cd) <= FP32_C_TOL
