@@ -168,7 +168,7 @@ void minor_dev_offsets(const MinorPlan& m, int upto, int* size, int* off) {
 // ---------------------------------------------------------------- FP32 e-graph arrays
 struct F32Offsets {
     bool used = false;
-    size_t steps[2], step_off[2], leaves[2], pk, sell_off, sell_w, sell, sellc, sell1, term_off, term2, term4, jmask;
+    size_t steps[2], step_off[2], leaves[2], pk, sell_off, sell_w, sell, sellc, sell1, term_off, term2, term4, jmask, b_pos;
 };
 
 // Walker count and leaf batch size that fit the kernel's shared memory: as many walkers
@@ -272,6 +272,22 @@ std::string add_f32(const HostPlan& h, const F32Shape& shape, Eg32Dev& v, Blob& 
         }
     }
     o.pk = b.add(pk);
+    // B row sets ordered by their G entry counts (descending, free index 0 first, then 1, ...,
+    // then by index), so that a slice's 32 row sets have similar widths for every free
+    // index (3He_II-s: 1.44x the entries in padded slots instead of 1.61x): the leaf stage's
+    // row b is B leaf-level row set order[b], and the B table is written in that order
+    std::vector<int32_t> order(nrb), b_pos(nrb);
+    {
+        auto cnt = [&](int rb, int j) { return e.B.n ? e.g_off[rb * nj + j + 1] - e.g_off[rb * nj + j] : 0; };
+        for (int rb = 0; rb < nrb; ++rb) order[rb] = rb;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            for (int j = 0; j < nj; ++j)
+                if (cnt(x, j) != cnt(y, j)) return cnt(x, j) > cnt(y, j);
+            return false;
+        });
+        for (int b = 0; b < nrb; ++b) b_pos[order[b]] = b;
+    }
+    o.b_pos = b.add(b_pos);
     // G entries in sliced-ELL form (FP32 weights); 4-byte entries (index | bf16 weight)
     // when every weight is real with at most 8 significant bits
     bool real = true, small = true;
@@ -295,7 +311,7 @@ std::string add_f32(const HostPlan& h, const F32Shape& shape, Eg32Dev& v, Blob& 
         for (int j = 0; j < nj; ++j) {
             int width = 0;
             for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
-                const int it = (sl * 32 + l) * nj + j;
+                const int it = order[sl * 32 + l] * nj + j;
                 width = std::max(width, e.g_off[it + 1] - e.g_off[it]);
             }
             soff.push_back((int32_t)rec);
@@ -306,7 +322,7 @@ std::string add_f32(const HostPlan& h, const F32Shape& shape, Eg32Dev& v, Blob& 
             if (real) sr.resize(rec + (size_t)width * 32, int2{0, 0});
             sc.resize(rec + (size_t)width * 32, int4{0, 0, 0, 0});
             for (int l = 0; l < 32 && sl * 32 + l < nrb; ++l) {
-                const int it = (sl * 32 + l) * nj + j;
+                const int it = order[sl * 32 + l] * nj + j;
                 for (int k = 0; k < e.g_off[it + 1] - e.g_off[it]; ++k) {
                     const int a = e.g_a[e.g_off[it] + k];
                     const float wr = (float)e.g_w[e.g_off[it] + k].real(), wi = (float)e.g_w[e.g_off[it] + k].imag();
@@ -394,6 +410,7 @@ void bind_f32(Eg32Dev& v, void* dev, const F32Offsets& o, float guard) {
     v.term2 = at<int2>(dev, o.term2);
     v.term4 = at<int4>(dev, o.term4);
     v.leaf_jmask = at<uint8_t>(dev, o.jmask);
+    v.b_pos = at<int32_t>(dev, o.b_pos);
     v.guard = guard;
 }
 

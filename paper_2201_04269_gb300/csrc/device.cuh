@@ -149,6 +149,10 @@ struct Eg32Dev {
     const int2* term2;               // real coefficients: (x, float bits of coef_j)
     const int4* term4;               // complex coefficients: (x, re bits, im bits, 0)
     const uint8_t* leaf_jmask;       // per A leaf: bit j set when a pair of the leaf has coef_j != 0
+    // B row sets in the order of the leaf stage (and of the site's B table): sorted by their
+    // G entry count, so that the 32 row sets of a sliced-ELL slice have similar widths;
+    // b_pos[e] = position of the B leaf level's row set e
+    const int32_t* b_pos;
     float guard;                     // a site whose error estimate exceeds this is recomputed
     int smem_bytes;                  // dynamic shared memory of the kernel
     int n_cols_a;                    // A leaves (column sets)

@@ -159,13 +159,14 @@ __device__ __forceinline__ void lap_node(const float2* M, const uint32_t* pk, in
 // A batch of leaves sharing one parent table: for every row set e the K parent values
 // (with the row-position signs) are loaded once and reused for each leaf of the batch.
 // Leaf l's table goes to out + l * n (A: shared memory) or, when to_cols, to
-// out + leaf * n (B: the site's B table, column-major by B column set).  A batch holds
+// out + leaf * n (B: the site's B table, column-major by B column set, row set e at
+// position opos[e]).  A batch holds
 // at most kMaxLeafBatch leaves; their columns, signs and output offsets stay in registers.
 constexpr int kMaxBatch = kMaxLeafBatch;
 template <int K>
 __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, int n, const WalkLeaf* lv,
                                            int nleaf, const float2* parent, float2* out, bool to_cols, int wt,
-                                           int n_parent, int64_t out_bound) {
+                                           int n_parent, int64_t out_bound, const int32_t* __restrict__ opos) {
     int col[kMaxBatch], obase[kMaxBatch];
     unsigned sm[kMaxBatch];
 #pragma unroll
@@ -182,6 +183,8 @@ __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, 
         }
     }
     for (int e = wt; e < n; e += kWalker) {
+        int eo = to_cols ? __ldg(opos + e) : e;
+        if (MBC_BAD(eo >= 0 && eo < n, 4, eo, n)) eo = e;
         float2 p[K];
         const float2* mr[K];
 #pragma unroll
@@ -197,7 +200,7 @@ __device__ __forceinline__ void lap_leaves(const float2* M, const uint32_t* pk, 
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < K; ++i) acc = cfma(acc, mr[i][col[l]], p[i]);
-                out[obase[l] + e] = flip_bits(acc, sm[l]);
+                out[obase[l] + eo] = flip_bits(acc, sm[l]);
             }
         }
     }
@@ -217,14 +220,14 @@ __device__ __forceinline__ void lap_node_k(int k, const float2* M, const uint32_
 
 __device__ __forceinline__ void lap_leaves_k(int k, const float2* M, const uint32_t* pk, int n, const WalkLeaf* lv,
                                              int nleaf, const float2* parent, float2* out, bool to_cols, int wt,
-                                             int n_parent, int64_t out_bound) {
+                                             int n_parent, int64_t out_bound, const int32_t* opos) {
     switch (k) {
-        case 1: lap_leaves<1>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
-        case 2: lap_leaves<2>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
-        case 3: lap_leaves<3>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
-        case 4: lap_leaves<4>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
-        case 5: lap_leaves<5>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
-        default: lap_leaves<6>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound); break;
+        case 1: lap_leaves<1>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound, opos); break;
+        case 2: lap_leaves<2>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound, opos); break;
+        case 3: lap_leaves<3>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound, opos); break;
+        case 4: lap_leaves<4>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound, opos); break;
+        case 5: lap_leaves<5>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound, opos); break;
+        default: lap_leaves<6>(M, pk, n, lv, nleaf, parent, out, to_cols, wt, n_parent, out_bound, opos); break;
     }
 }
 
@@ -395,7 +398,7 @@ __device__ __forceinline__ void walk(const Eg32Dev& d, const WalkDev& f, bool is
             const WalkLeaf* lv = f.leaves + st.leaf0;
             lap_leaves_k(n, M, spk + f.pk_off[n], f.size[n], lv, st.nleaf, stack + f.off[n - 1],
                          is_a ? leafbuf : bt, !is_a, wt, f.size[n - 1],
-                         is_a ? (int64_t)d.leafbuf_vals : (int64_t)d.n_cols_b * d.n_rows_b);
+                         is_a ? (int64_t)d.leafbuf_vals : (int64_t)d.n_cols_b * d.n_rows_b, d.b_pos);
             walker_sync(w);
             if (is_a) leaf_stage<REAL, NJ>(d, lv, st.nleaf, leafbuf, f.size[n], bt, acc, guard, wt);
         }
