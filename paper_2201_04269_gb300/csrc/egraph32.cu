@@ -608,16 +608,19 @@ __global__ void __launch_bounds__(768, 1) egraph32_batch_kernel(const BatchItem3
 // is close to a complex Gaussian of rms r sqrt(sum_x s_x^2), r the rms ratio of a site's
 // FP32 error to s_x, measured 1.5e-7 on the He-3 workloads; kSliceErr = 1.67 r.  It is an
 // estimate, not a bound: 4e-7 (2.67 r) recomputed three times as many slices of the He-3
-// workload at 24^3 x 48 without changing its largest C(t) error, 8.2e-7), and when
-// err(t) > tol |C(t)| every site of the slice that is not recomputed already is appended
-// to the recompute list.  C(t) here is the FP32 estimate with the momentum phase of the
-// site sum.
+// workload at 24^3 x 48 without changing its largest C(t) error, 8.2e-7).  When
+// err(t) > tol |C(t)|, the sites of the slice with the largest s_x are appended to the
+// recompute list -- those with s_x above the largest threshold tau for which the sites at
+// or below tau leave an estimate of at most tol |C(t)| / 2 (a recomputed site carries no
+// FP32 error; tau by bisection) -- skipping sites the site guard listed already (s_x = 0).
+// C(t) here is the FP32 estimate with the momentum phase of the site sum.
 constexpr double kSliceErr = 2.5e-7;
+constexpr int kTauSteps = 40;
 __device__ __forceinline__ void slice_guard_body(const d4* __restrict__ part, const double* __restrict__ scale,
                                                  int64_t st, int64_t V3, Momentum mom, double tol, int64_t unit0,
                                                  unsigned int* __restrict__ flag_count,
                                                  unsigned int* __restrict__ flag_list, unsigned int flag_cap, double* red,
-                                                 int* s_flag) {
+                                                 int* s_flag, double* s_tau) {
     double re = 0.0, im = 0.0, m = 0.0;
     for (int64_t x = threadIdx.x; x < V3; x += blockDim.x) {
         const d4 v = part[st * V3 + x];
@@ -647,19 +650,43 @@ __device__ __forceinline__ void slice_guard_body(const d4* __restrict__ part, co
         }
     kacc kq, kz;
     block_sum(cd_make(q, 0.0), kq, kz, red);
+    // the remaining sum of (s_x / m)^2 allowed after the recompute: (tol |C| / (2 kSliceErr m))^2
+    __shared__ double s_allow;
     if (threadIdx.x == 0) {
         const double cr = kr.hi + kr.lo, ci = ki.hi + ki.lo;
+        const double cabs = sqrt(cr * cr + ci * ci);
         const double err = kSliceErr * m * sqrt(kq.hi + kq.lo);
-        *s_flag = m > 0.0 && !(err <= tol * sqrt(cr * cr + ci * ci));
+        *s_flag = m > 0.0 && !(err <= tol * cabs);
+        const double a = m > 0.0 ? tol * cabs / (2.0 * kSliceErr * m) : 0.0;
+        s_allow = isfinite(a) ? a * a : 0.0;
+        s_tau[0] = 0.0;                              // sum over s_x <= tau within the allowance
+        s_tau[1] = 1.0;                              // (every site: above it)
     }
     __syncthreads();
-    if (*s_flag)
-        for (int64_t x = threadIdx.x; x < V3; x += blockDim.x)
-            if (scale[st * V3 + x] > 0.0) {
-                const unsigned k = atomicAdd(flag_count, 1u);
-                if (!MBC_BAD(k < flag_cap, 31, k, flag_cap)) flag_list[k] = (unsigned int)(unit0 + st * V3 + x);
-            }
-    __syncthreads();
+    if (!*s_flag) return;
+    for (int it = 0; it < kTauSteps; ++it) {
+        const double mid = 0.5 * (s_tau[0] + s_tau[1]);
+        double qb = 0.0;
+        for (int64_t x = threadIdx.x; x < V3; x += blockDim.x) {
+            const double r = scale[st * V3 + x] / m;
+            if (r <= mid) qb += r * r;
+        }
+        kacc kb, kbz;
+        block_sum(cd_make(qb, 0.0), kb, kbz, red);
+        if (threadIdx.x == 0) {
+            if (kb.hi + kb.lo <= s_allow) s_tau[0] = mid;
+            else s_tau[1] = mid;
+        }
+        __syncthreads();
+    }
+    const double tau = s_tau[0];
+    for (int64_t x = threadIdx.x; x < V3; x += blockDim.x) {
+        const double sx = scale[st * V3 + x];
+        if (sx > 0.0 && sx / m > tau) {
+            const unsigned k = atomicAdd(flag_count, 1u);
+            if (!MBC_BAD(k < flag_cap, 31, k, flag_cap)) flag_list[k] = (unsigned int)(unit0 + st * V3 + x);
+        }
+    }
 }
 
 __global__ void slice_guard_kernel(const d4* __restrict__ part, const double* __restrict__ scale, int64_t V3,
@@ -667,7 +694,8 @@ __global__ void slice_guard_kernel(const d4* __restrict__ part, const double* __
                                    unsigned int* __restrict__ flag_list, unsigned int flag_cap) {
     __shared__ double red[4 * 32];
     __shared__ int s_flag;
-    slice_guard_body(part, scale, blockIdx.x, V3, mom, tol, 0, flag_count, flag_list, flag_cap, red, &s_flag);
+    __shared__ double s_tau[2];
+    slice_guard_body(part, scale, blockIdx.x, V3, mom, tol, 0, flag_count, flag_list, flag_cap, red, &s_flag, s_tau);
 }
 
 // Batched slice guard: block b is slice b - slice_begin of the item whose slices contain it.
@@ -676,6 +704,7 @@ __global__ void slice_guard_batch_kernel(const BatchItem32* __restrict__ items, 
                                          unsigned int flag_cap) {
     __shared__ double red[4 * 32];
     __shared__ int s_flag;
+    __shared__ double s_tau[2];
     int lo = 0, hi = n_items - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -684,7 +713,7 @@ __global__ void slice_guard_batch_kernel(const BatchItem32* __restrict__ items, 
     const BatchItem32& it = items[lo];
     if (std::isinf(it.slice_tol) && it.slice_tol > 0) return;
     slice_guard_body(it.part, it.scale, (int64_t)blockIdx.x - it.slice_begin, it.g.V3, Momentum(), it.slice_tol,
-                     it.unit_begin, flag_count, flag_list, flag_cap, red, &s_flag);
+                     it.unit_begin, flag_count, flag_list, flag_cap, red, &s_flag, s_tau);
 }
 
 // Cluster launch of kern with as many clusters as can be resident at once (at most
