@@ -206,7 +206,11 @@ mbc_status mbc_correlator_host(mbc_plan* plan, const void* U_host, const void* D
  * table (synchronously); mbc_batch with the same item array (same plans, pointers and
  * sizes) then allocates nothing and can be captured in a CUDA graph.  Called with other
  * items outside a capture, mbc_batch reserves them first; inside a capture it fails
- * with MBC_OOM. */
+ * with MBC_OOM.  MBC_PREC_FP32 items run as one FP32 launch over all their units (with
+ * the largest walker count and cluster size among them; items of fewer leave warps or
+ * blocks idle), one slice-guard launch and one double-float launch over the units the
+ * guards list; a plan whose guard settings or kernel shape changed since the
+ * reservation is reserved again (MBC_OOM inside a capture, as above). */
 typedef struct {
     mbc_plan* plan;
     const void* U;
@@ -239,8 +243,10 @@ mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_strea
  *    error of a 97k-site sample below 1e-6.  +inf recomputes no site, <= 0 every site.
  *  - per time slice (always): the error of C(t) from the FP32 sites is estimated as
  *    2.5e-7 x sqrt(sum_x s_x^2) (independent rounding errors), and when that exceeds
- *    slice_tolerance x |C(t)| (with the sink momentum phase, if any) every remaining
- *    FP32 site of the slice is recomputed.  Default 1e-6; +inf switches it off.
+ *    slice_tolerance x |C(t)| (with the sink momentum phase, if any) the slice's FP32
+ *    sites of largest s_x are recomputed: those above the largest threshold for which
+ *    the sites left in FP32 estimate at most half the tolerance.  Default 1e-6; +inf
+ *    switches it off.
  *
  * mbc_plan_set_guard / mbc_plan_get_guard: the plan's site threshold and slice tolerance
  * (host calls, effective for evaluations issued afterwards).  mbc_fp32_recomputed: the

@@ -609,6 +609,28 @@ def test_fp32_general_problems(ctx):
         plan.destroy()
 
 
+def test_fp32_empty_ragged_and_multiset(ctx):
+    """MBC_PREC_FP32 on a ragged slice (37 sites), fewer sites than blocks (5), an empty lattice,
+    and two sets in one call bit-identical to two separate calls."""
+    plan = ctx.plan_operator("he3_I", "egraph", "fp32")
+    U, D = mi.workload_fields("he3_24x48", L=4, t_list=[0, 7])
+    for nv in (37, 5):
+        C, S = run(plan, U[None, :, :nv], D[None, :, :nv])
+        ref = oracle_sites("he3_I", U[:, :nv], D[:, :nv]).reshape(2, nv)
+        check(S[0], ref, "fp32")
+        assert relerr(C[0], ref.sum(axis=1)) <= FP32_C_TOL
+    Z = np.zeros((1, 2, 0, 12, 12), complex)
+    C, S = run(plan, Z, Z)
+    assert np.all(C == 0)
+    U3 = np.stack([U[:, :37], U[::-1, :37].copy()])
+    D3 = np.stack([D[:, :37], D[::-1, :37].copy()])
+    C2, _ = run(plan, U3, D3)
+    Ca, _ = run(plan, U3[:1], D3[:1])
+    Cb, _ = run(plan, U3[1:], D3[1:])
+    assert np.array_equal(C2[0], Ca[0]) and np.array_equal(C2[1], Cb[0])
+    plan.destroy()
+
+
 def test_fp32_vanishing_and_rejections(ctx):
     from paper_2201_04269_gb300 import abi
     U, D = mi.workload_fields("dinucleon_16x32", L=2, T=2)
