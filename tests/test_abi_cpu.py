@@ -276,3 +276,27 @@ def test_minor_egraph_size_and_flops(abi, hctx, name):
     assert info["flops_per_site"] < abi.mbc_plan_get_info(tree_plan)["flops_per_site"]
     abi.mbc_plan_destroy(plan)
     abi.mbc_plan_destroy(tree_plan)
+
+
+def test_fp32_plan_settings_on_the_host(abi, hctx):
+    """MBC_PREC_FP32 plans on a host-only context: FP32 is accepted only for the e-graph
+    algorithm; guard settings round-trip (NaN rejected); kernel shapes are validated
+    (threads a multiple of 128 up to 768, one or two blocks per site, leaf batch 1..3)."""
+    plan, _ = plan_of(abi, hctx, "he3_II_s", "egraph", "fp32")
+    assert abi.mbc_plan_get_guard(plan) == (2.0, 1e-6)
+    abi.mbc_plan_set_guard(plan, 3.5, 2e-6, hctx)
+    assert abi.mbc_plan_get_guard(plan) == (3.5, 2e-6)
+    with pytest.raises(abi.MbcError) as e:
+        abi.mbc_plan_set_guard(plan, float("nan"), 1e-6, hctx)
+    assert e.value.status == 1
+    assert abi.mbc_plan_get_guard(plan) == (3.5, 2e-6)
+    for bad in ((100, 1, 3), (896, 1, 3), (640, 3, 3), (640, 1, 4), (640, 0, 1)):
+        with pytest.raises(abi.MbcError):
+            abi.mbc_set_schedule(plan, *bad, ctx=hctx)
+    abi.mbc_set_schedule(plan, 512, 2, 2, ctx=hctx)
+    assert abi.mbc_get_schedule(plan) == dict(threads=512, blocks_per_sm=2, sites_per_unit=2)
+    for algo in ("direct", "tree"):
+        with pytest.raises(abi.MbcError) as e:
+            plan_of(abi, hctx, "proton", algo, "fp32")
+        assert e.value.status == 2                          # MBC_UNSUPPORTED
+    abi.mbc_plan_destroy(plan)
