@@ -194,7 +194,10 @@ mbc_status mbc_correlator_momentum(mbc_plan* plan, const void* U, const void* D,
 
 /* End to end from host memory: copies U, D (host, pinned or pageable, same layout) to
  * the context's device buffers, evaluates, copies C back to host memory C_host, on
- * the given stream, and synchronises that stream before returning. */
+ * the given stream, and synchronises that stream before returning.  Large calls are
+ * split into up to 8 chunks of whole time slices: the copy of a chunk runs on a second
+ * stream of the context while the previous chunk is evaluated on the given one (pinned
+ * host memory lets the copies overlap); the results equal a single evaluation. */
 mbc_status mbc_correlator_host(mbc_plan* plan, const void* U_host, const void* D_host, int n_sets, int T,
                                int64_t V3, void* C_host, mbc_stream stream);
 
@@ -251,7 +254,8 @@ mbc_status mbc_batch(mbc_ctx* ctx, const mbc_work* items, int n_items, mbc_strea
  * mbc_plan_set_guard / mbc_plan_get_guard: the plan's site threshold and slice tolerance
  * (host calls, effective for evaluations issued afterwards).  mbc_fp32_recomputed: the
  * number of sites that the last MBC_PREC_FP32 evaluation of this context recomputed
- * (synchronises the device; 0 if none ran).  Results are bit-reproducible for a given
+ * (synchronises the device; 0 if none ran; after a chunked mbc_correlator_host, its
+ * last chunk's).  Results are bit-reproducible for a given
  * plan, guards, sizes and device.
  * ---------------------------------------------------------------------------------- */
 mbc_status mbc_plan_set_guard(mbc_plan* plan, double site_threshold, double slice_tolerance);

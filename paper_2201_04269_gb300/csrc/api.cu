@@ -884,8 +884,15 @@ void mbc_destroy(mbc_ctx* c) {
     }
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    for (mbc_plan* p : c->plans) { if (p->dev) cudaFree(p->dev); delete p; }
+    for (mbc_plan* p : c->plans) {
+        if (p->dev) cudaFree(p->dev);
+        if (p->dev32) cudaFree(p->dev32);
+        delete p;
+    }
     destroy_block_plans(c);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->h2d_start) cudaEventDestroy(c->h2d_start);
+    for (cudaEvent_t ev : c->h2d_done) if (ev) cudaEventDestroy(ev);
     Buf* bufs[] = {&c->partials, &c->site_tmp, &c->scratch, &c->exps, &c->counter, &c->hU, &c->hD, &c->hC,
                    &c->batch_items, &c->batch_parts, &c->batch_k, &c->blk_part, &c->blk_F, &c->blk_tree,
                    &c->bslot, &c->flags, &c->gscale, &c->batch32_items, &c->batch32_scale};
@@ -1120,13 +1127,56 @@ mbc_status mbc_correlator_host(mbc_plan* P, const void* U_host, const void* D_ho
     if (st == MBC_OK) st = ensure(c, c->hC, cb, s);
     if (st != MBC_OK) return st;
     cudaError_t e = cudaSuccess;
-    if (fb) {
-        e = cudaMemcpyAsync(c->hU.p, U_host, fb, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c->hD.p, D_host, fb, cudaMemcpyHostToDevice, s);
+    // the time slices in up to kHostChunks chunks: the copy of chunk k + 1 (on the copy
+    // stream) overlaps the evaluation of chunk k (on the caller's stream); a chunk is
+    // evaluated as its own slices, so the results equal one evaluation of all of them
+    const int64_t n_slices = (int64_t)n_sets * T;
+    int chunks = (int)std::min<int64_t>(mbc_ctx::kHostChunks, n_slices);
+    if (n_sites < (int64_t)c->sms * 64) chunks = 1;             // too small to gain from overlap
+    if (fb && chunks > 1) {
+        if (!c->copy_stream) {
+            e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->h2d_start, cudaEventDisableTiming);
+            for (int k = 0; k < mbc_ctx::kHostChunks && e == cudaSuccess; ++k)
+                e = cudaEventCreateWithFlags(&c->h2d_done[k], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(c, e, "copy stream");
+        }
+        // the copies wait for the caller's earlier work on s
+        e = cudaEventRecord(c->h2d_start, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->h2d_start, 0);
+        const size_t per_slice = sizeof(double) * 288 * (size_t)V3;
+        for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
+            const int64_t a = n_slices * k / chunks, b = n_slices * (k + 1) / chunks;
+            const size_t off = per_slice * (size_t)a, len = per_slice * (size_t)(b - a);
+            e = cudaMemcpyAsync((char*)c->hU.p + off, (const char*)U_host + off, len, cudaMemcpyHostToDevice,
+                                c->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((char*)c->hD.p + off, (const char*)D_host + off, len, cudaMemcpyHostToDevice,
+                                    c->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->h2d_done[k], c->copy_stream);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "host to device copy");
+        for (int k = 0; k < chunks; ++k) {
+            const int64_t a = n_slices * k / chunks, b = n_slices * (k + 1) / chunks;
+            const size_t off = per_slice * (size_t)a;
+            e = cudaStreamWaitEvent(s, c->h2d_done[k], 0);
+            if (e != cudaSuccess) return cuda_fail(c, e, "stream wait");
+            st = run(P, (const char*)c->hU.p + off, (const char*)c->hD.p + off, 1, (int)(b - a), V3,
+                     (double2*)c->hC.p + a, nullptr, s);
+            if (st != MBC_OK) {
+                cudaStreamSynchronize(c->copy_stream);
+                return st;
+            }
+        }
+    } else {
+        if (fb) {
+            e = cudaMemcpyAsync(c->hU.p, U_host, fb, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->hD.p, D_host, fb, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(c, e, "host to device copy");
+        }
+        st = run(P, c->hU.p, c->hD.p, n_sets, T, V3, c->hC.p, nullptr, s);
+        if (st != MBC_OK) return st;
     }
-    st = run(P, c->hU.p, c->hD.p, n_sets, T, V3, c->hC.p, nullptr, s);
-    if (st != MBC_OK) return st;
     if (cb) {
         e = cudaMemcpyAsync(C_host, c->hC.p, cb, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "device to host copy");

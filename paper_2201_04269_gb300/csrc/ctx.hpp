@@ -25,6 +25,10 @@ struct mbc_ctx {
     int64_t launches = 0;
     int sms = 0;
     mbc::Buf partials, site_tmp, scratch, exps, counter, hU, hD, hC;
+    // mbc_correlator_host: a copy stream and one event per slice chunk (created on first use)
+    static constexpr int kHostChunks = 8;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t h2d_start = nullptr, h2d_done[kHostChunks] = {};
     std::vector<mbc_plan*> plans;
     std::vector<mbc_block_plan*> block_plans;
     std::map<std::string, mbc_schedule> tune_cache;
