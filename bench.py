@@ -621,7 +621,7 @@ def run_local(args, rank, world, local):
         del U_pin, D_pin
 
     cpu, accuracy = None, None
-    if rank == 0 and headline and not args.no_cpu:
+    if rank == 0 and world == 1 and headline and not args.no_cpu:
         cpu, _, (pts, ref) = cpu_baseline()
         # per-site values of the headline plan (per-site guard active) on the sampled sites
         S = torch.zeros(n_sets, n_t, n_v, dtype=torch.complex128, device="cuda")
