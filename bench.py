@@ -217,7 +217,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{OPERATOR} (stand-in for He-3 II) {L}^3x{T}, one source, oracle on a sample"},
+            "config": {"workload": f"{OPERATOR} (stand-in for He-3 II) {L}^3x{T}, 1 source(s) per GPU",
+                       "algorithm": "oracle (canonical merged form, plain C, OpenMP over sites) on a bounded sample "
+                                    "of the workload's sites", "arithmetic": "fp64"},
             "cpu_baseline": meta, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                           "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -651,8 +653,9 @@ def run_local(args, rank, world, local):
         config = {"workload": (f"{args.op}" + (" (stand-in for He-3 II)" if args.op == OPERATOR else "") +
                                f" {Lb}^3x{Tb}" + (f" ({n_t} slices)" if n_t != Tb else "") +
                                (f" ({n_v} sites/slice)" if n_v != Lb ** 3 else "") +
-                               f", {n_sets} source(s) per GPU, {args.algo} plan, {args.prec}" +
+                               f", {n_sets} source(s) per GPU" +
                                (f", noise {args.noise}, kappa {args.kappa}" if args.noise else "")),
+                  "algorithm": f"{args.algo} plan", "arithmetic": args.prec,
                   "sites_per_gpu": n_sites,
                   "l2": f"inputs {field_bytes / 1e9:.2f} GB per GPU" +
                         (", larger than L2" if field_bytes > 129e6 else ", smaller than L2"),
