@@ -326,7 +326,9 @@ mbc_status mbc_get_schedule(const mbc_plan* plan, mbc_schedule* s);
  * per-site partial sums, the kernel's K slots) taken from one fixed device array of
  * MBC_NOALLOC_SCRATCH_BYTES bytes built into the library; it calls no cudaMalloc,
  * cudaFree or other allocating routine.  (MBC_PREC_FP32 plans are evaluated here in
- * the double-float arithmetic of MBC_PREC_MIXED.)  The caller still supplies the fields
+ * the double-float arithmetic of MBC_PREC_MIXED, so their results agree with
+ * mbc_correlator's to the FP32 path's tolerance, not bit for bit; for the other plans
+ * they are identical.)  The caller still supplies the fields
  * U, D and the output C (device memory, same layouts as mbc_correlator); the plan must
  * have been created beforehand (plan creation allocates).
  *  - Every GPU that loads this part of the library holds the array until the process
