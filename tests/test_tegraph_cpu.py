@@ -129,3 +129,21 @@ def test_rejects_malformed_expressions(hctx):
     for bad in ("", "T(i,j", "T(i,i,i) S(i)", "T()"):
         with pytest.raises(abi.MbcError):
             abi.mbc_tensor_egraph(hctx, bad, "eps", 1000, 3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_enode_limit_matches_oracle(hctx, seed):
+    """Saturation stopped by the e-node limit (Sec. 5) leaves the same e-graph size as the
+    oracle's with the same limit, and the extracted cost is the oracle's."""
+    from paper_2201_04269_gb300 import abi
+    rng = random.Random(100 + seed)
+    E = random_network(rng, rng.choice([3, 4]))
+    for lim in (2, 4, 7, 12, 30):
+        g = oe.TensorEGraph(antisym=("eps",), node_limit=lim)
+        r, _, _ = g.add_expr(E)
+        g.saturate(r)
+        best, cost = g.extract()
+        plan, (nc, nn) = abi.mbc_tensor_egraph(hctx, text(E), "eps", lim, 3)
+        assert (nc, nn) == (len(g.classes), g.n_nodes), (lim, E)
+        root, _, classes = parse(plan)
+        assert classes[root][1] == cost[r], (lim, E)
