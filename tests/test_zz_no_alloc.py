@@ -80,3 +80,26 @@ def test_noalloc_rejects_oversized_requests(ctx):
     plan.destroy()
     tree.destroy()
     zero.destroy()
+
+
+def test_noalloc_fp32_plan_uses_double_float(ctx):
+    """An MBC_PREC_FP32 plan through the allocation-free entry point is evaluated in
+    double-float: C(t) agrees with the pooled FP32 call to the FP32 target (1e-6) and with
+    the double-float plan to 1e-12."""
+    from paper_2201_04269_gb300 import abi
+    U, D = fields("he3_24x48", L=6, t_list=[3, 30])
+    n_sets, T, V3 = U.shape[:3]
+    p32 = ctx.plan_operator("he3_I", "egraph", "fp32")
+    pdf = ctx.plan_operator("he3_I", "egraph", "mixed")
+    C32 = torch.zeros(n_sets, T, dtype=torch.complex128, device="cuda")
+    Cdf = torch.zeros_like(C32)
+    p32.correlator(U, D, C32)
+    pdf.correlator(U, D, Cdf)
+    C = torch.zeros_like(C32)
+    abi.mbc_correlator_noalloc(p32.handle, U, D, n_sets, T, V3, C, ctx=ctx.handle)
+    torch.cuda.synchronize()
+    got, ref32, refdf = C.cpu().numpy(), C32.cpu().numpy(), Cdf.cpu().numpy()
+    assert np.max(np.abs(got - ref32) / np.abs(ref32)) <= 1e-6
+    assert np.max(np.abs(got - refdf) / np.abs(refdf)) <= 1e-12
+    p32.destroy()
+    pdf.destroy()
