@@ -833,8 +833,11 @@ bool noalloc_view(mbc_plan* P, NoallocView* v) {
     v->device = P->ctx->device;
     v->algo = P->hp.algo;
     v->prec = P->hp.prec;
-    v->threads = P->sched.threads;
-    v->blocks_per_sm = P->sched.blocks_per_sm;
+    // an MBC_PREC_FP32 plan is evaluated by the double-float kernel, with that kernel's
+    // schedule (its own schedule is the FP32 kernel's shape)
+    const mbc_schedule& sc = P->hp.prec == MBC_PREC_FP32 ? P->sched_df : P->sched;
+    v->threads = sc.threads;
+    v->blocks_per_sm = sc.blocks_per_sm;
     v->sms = P->ctx->sms;
     v->scale = cd_make(P->hp.scale.real(), P->hp.scale.imag());
     v->ed = P->ed;
