@@ -282,6 +282,30 @@ def test_plan_file_and_determinism(ctx, tmp_path):
     plan2.destroy()
 
 
+def test_fp32_plan_file_guards_and_shapes(ctx, tmp_path):
+    """An MBC_PREC_FP32 plan saved and loaded evaluates bit for bit as the original (the FP32
+    view is rebuilt from the file's plan); the loaded plan starts from the default guards;
+    a kernel shape set on the loaded plan gives the same values as on the original."""
+    from paper_2201_04269_gb300 import abi
+    U, D = mi.workload_fields("he3_24x48", L=4, t_list=[2, 11])
+    plan = ctx.plan_operator("he3_I", "egraph", "fp32")
+    C1, S1 = run(plan, U[None], D[None])
+    p = str(tmp_path / "f.plan")
+    plan.save(p)
+    plan2 = ctx.load_plan(p)
+    assert plan2.guard == (2.0, 1e-6)
+    C2, S2 = run(plan2, U[None], D[None])
+    assert np.array_equal(C1, C2) and np.array_equal(S1, S2)
+    for pl in (plan, plan2):
+        abi.mbc_set_schedule(pl.handle, 512, 1, 2)
+    C3, S3 = run(plan, U[None], D[None])
+    C4, S4 = run(plan2, U[None], D[None])
+    assert np.array_equal(C3, C4) and np.array_equal(S3, S4)
+    check(S3[0], oracle_sites("he3_I", U, D).reshape(S3[0].shape), "fp32")
+    plan.destroy()
+    plan2.destroy()
+
+
 def test_batch_matches_separate_calls(ctx):
     from paper_2201_04269_gb300 import abi
     items, refs, keep = [], [], []
