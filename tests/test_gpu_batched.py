@@ -141,6 +141,32 @@ def test_fp32_batch_recompute_interleaved_plans(ctx):
         p.destroy()
 
 
+def test_batch_mixing_all_three_arithmetics(ctx):
+    """FP64, double-float and FP32 items in one mbc_batch (one launch per precision, the
+    FP32 launch with its guards and recompute): each item's C equals its own call."""
+    from paper_2201_04269_gb300 import abi
+    L, T = 4, 3
+    U, D = mi.workload_fields("batched_64", set_index=5, L=L, T=T)
+    Ud, Dd = torch.from_numpy(U[None]).cuda(), torch.from_numpy(D[None]).cuda()
+    plans, items, keep = [], [], []
+    for op in ("dinucleon_I", "he3_I"):
+        for prec in ("fp64", "mixed", "fp32"):
+            pl = ctx.plan_operator(op, "egraph", prec)
+            C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+            keep.append(C)
+            plans.append(pl)
+            items.append(dict(plan=pl.handle, U=Ud, D=Dd, C=C, site_out=None, n_sets=1, T=T, V3=L ** 3))
+    ctx.batch(items)
+    torch.cuda.synchronize()
+    for it, pl in zip(items, plans):
+        C1 = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+        pl.correlator(Ud, Dd, C1)
+        torch.cuda.synchronize()
+        assert relerr(it["C"].cpu().numpy(), C1.cpu().numpy()) <= 1e-12
+    for pl in plans:
+        pl.destroy()
+
+
 def test_batched_workload_64_sets_full_size(ctx):
     """The batched workload at its stated size in one persistent FP32 launch (plus its
     guard, recompute and site-sum launches): three sampled sites of every item against
