@@ -592,6 +592,15 @@ def test_fp32_matches_oracle(ctx, name, wl, kw):
     Ci, Si = run(plan, U[None], D[None])
     assert ctx.fp32_recomputed == 0
     check(Si[0], ref, "fp32")
+    # slice tolerance 0 (site guard off): the slice guard lists every site of every slice
+    plan.set_guard(float("inf"), 0.0)
+    Ud, Dd = dev(U[None]), dev(D[None])
+    Cz = torch.zeros(1, U.shape[0], dtype=torch.complex128, device="cuda")
+    plan.correlator(Ud, Dd, Cz)
+    torch.cuda.synchronize()
+    assert ctx.fp32_recomputed == n
+    e = relerr(Cz.cpu().numpy()[0], ref.sum(axis=1))
+    assert e <= TIGHT_MIXED, e
     plan.destroy()
 
 
