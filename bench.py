@@ -182,7 +182,7 @@ def cpu_baseline(n_sites_target=None, seconds=20.0):
     threads = native.max_threads()
     rng = np.random.default_rng(0)
     # calibrate on a few sites, then size the sample to ~`seconds` of wall time
-    probe = [(t, int(rng.integers(L ** 3))) for t in rng.choice(T, size=max(threads, 4))]
+    probe = [(t, int(rng.integers(L ** 3))) for t in rng.choice(T, size=max(8 * threads, 16))]
 
     def regen(pts):
         U = np.concatenate([mi.site_matrices(SEED, 0, 0, t, [x], KAPPA) for t, x in pts])
@@ -190,6 +190,7 @@ def cpu_baseline(n_sites_target=None, seconds=20.0):
         return U, D
 
     U, D = regen(probe)
+    plan.site_values(U[:threads], D[:threads], n_threads=threads)      # warm-up (threads, first-call costs)
     t0 = time.perf_counter()
     plan.site_values(U, D, n_threads=threads)
     dt = time.perf_counter() - t0
