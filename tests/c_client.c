@@ -5,8 +5,10 @@
  *
  * usage: c_client <device> [<fields file> <T> <V3>]
  *   fields file: U then D, complex double [T][V3][12][12] each (raw, little endian)
- * output lines: "terms <n>", "canonical <n>", then "C <t> <re> <im>" and
- * "H <t> <re> <im>" (device and host-buffer results) when a device is given.
+ * output lines: "terms <n>", "canonical <n>", "guard <site threshold> <slice tolerance>"
+ * and "shape <threads> <blocks per site> <leaf batch>" of an MBC_PREC_FP32 plan after
+ * setting them, then "C <t> <re> <im>", "H <t> <re> <im>" (FP64, device and host-buffer
+ * results) and "F <t> <re> <im>" (FP32 with guards) when a device is given.
  */
 #include <stdint.h>
 #include <stdio.h>
@@ -52,6 +54,16 @@ int main(int argc, char** argv) {
     mbc_plan_info info;
     if (mbc_plan_get_info(plan, &info) != MBC_OK) return die(ctx, "mbc_plan_get_info");
     printf("canonical %lld\n", (long long)info.canonical_terms);
+    mbc_plan* p32 = NULL;
+    if (mbc_plan_create(ctx, &pr, MBC_ALGO_EGRAPH, MBC_PREC_FP32, &p32) != MBC_OK) return die(ctx, "FP32 plan");
+    if (mbc_plan_set_guard(p32, 3.0, 5e-7) != MBC_OK) return die(ctx, "mbc_plan_set_guard");
+    double g_site = 0.0, g_slice = 0.0;
+    if (mbc_plan_get_guard(p32, &g_site, &g_slice) != MBC_OK) return die(ctx, "mbc_plan_get_guard");
+    printf("guard %g %g\n", g_site, g_slice);
+    mbc_schedule sh = {384, 1, 2};
+    if (mbc_set_schedule(p32, &sh) != MBC_OK) return die(ctx, "mbc_set_schedule");
+    if (mbc_get_schedule(p32, &sh) != MBC_OK) return die(ctx, "mbc_get_schedule");
+    printf("shape %d %d %d\n", sh.threads, sh.blocks_per_sm, sh.sites_per_unit);
 
     if (device >= 0 && argc >= 5) {
         const int T = atoi(argv[3]);
@@ -73,10 +85,14 @@ int main(int argc, char** argv) {
         for (int t = 0; t < T; ++t) printf("C %d %.17g %.17g\n", t, c[2 * t], c[2 * t + 1]);
         if (mbc_correlator_host(plan, h, h + n, 1, T, V3, c, NULL) != MBC_OK) return die(ctx, "mbc_correlator_host");
         for (int t = 0; t < T; ++t) printf("H %d %.17g %.17g\n", t, c[2 * t], c[2 * t + 1]);
+        if (mbc_correlator(p32, U, D, 1, T, V3, C, NULL, NULL) != MBC_OK) return die(ctx, "FP32 mbc_correlator");
+        if (cudaMemcpy(c, C, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost) != cudaSuccess) return 6;
+        for (int t = 0; t < T; ++t) printf("F %d %.17g %.17g\n", t, c[2 * t], c[2 * t + 1]);
         cudaFree(U); cudaFree(D); cudaFree(C);
         free(c);
         free(h);
     }
+    mbc_plan_destroy(p32);
     mbc_plan_destroy(plan);
     mbc_destroy(ctx);
     free(idx); free(w); free(off); free(proj);

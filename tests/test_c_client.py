@@ -1,6 +1,7 @@
 """The C ABI used from plain C (tests/c_client.c, built with gcc against include/mbc.h and
-libmbc.so): planning in a host-only context on the CPU, and a proton correlator on the GPU
-checked against the oracle."""
+libmbc.so): planning in a host-only context on the CPU (FP32 guard and shape settings
+included), and a proton correlator on the GPU in FP64 and in FP32 with guards checked
+against the oracle."""
 import os
 import subprocess
 
@@ -42,6 +43,8 @@ def test_c_client_plans_on_the_host(client):
     op = oops.build("proton")
     assert out[0] == f"terms {sum(len(t) for t in op.terms)}"
     assert out[1] == f"canonical {ocor.CanonicalPlan(op).n_terms}"
+    assert out[2] == "guard 3 5e-07"
+    assert out[3] == "shape 384 1 2"
 
 
 @pytest.mark.gpu
@@ -57,7 +60,7 @@ def test_c_client_evaluates_on_the_gpu(client, tmp_path):
         f.write(np.ascontiguousarray(D).tobytes())
     out = run(client, 0, path, T, V3)
     want = ocor.correlator(ocor.CanonicalPlan(oops.build("proton")).site_values, U, D)
-    for tag in ("C", "H"):
+    for tag, tol in (("C", 1e-12), ("H", 1e-12), ("F", 5e-7)):
         got = np.array([complex(float(l.split()[2]), float(l.split()[3])) for l in out if l.startswith(tag + " ")])
         assert len(got) == T
-        assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-12
+        assert np.max(np.abs(got - want) / np.abs(want)) <= tol, tag
