@@ -1137,12 +1137,20 @@ mbc_status mbc_correlator_host(mbc_plan* P, const void* U_host, const void* D_ho
     int chunks = (int)std::min<int64_t>(mbc_ctx::kHostChunks, n_slices);
     if (n_sites < (int64_t)c->sms * 64) chunks = 1;             // too small to gain from overlap
     if (fb && chunks > 1) {
-        if (!c->copy_stream) {
-            e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->h2d_start, cudaEventDisableTiming);
-            for (int k = 0; k < mbc_ctx::kHostChunks && e == cudaSuccess; ++k)
-                e = cudaEventCreateWithFlags(&c->h2d_done[k], cudaEventDisableTiming);
-            if (e != cudaSuccess) return cuda_fail(c, e, "copy stream");
+        if (!c->copy_stream) {          // created once, all or nothing
+            cudaStream_t cs = nullptr;
+            cudaEvent_t ev[mbc_ctx::kHostChunks + 1] = {};
+            e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            for (int k = 0; k <= mbc_ctx::kHostChunks && e == cudaSuccess; ++k)
+                e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                for (cudaEvent_t x : ev) if (x) cudaEventDestroy(x);
+                if (cs) cudaStreamDestroy(cs);
+                return cuda_fail(c, e, "copy stream");
+            }
+            c->copy_stream = cs;
+            c->h2d_start = ev[mbc_ctx::kHostChunks];
+            for (int k = 0; k < mbc_ctx::kHostChunks; ++k) c->h2d_done[k] = ev[k];
         }
         // the copies wait for the caller's earlier work on s
         e = cudaEventRecord(c->h2d_start, s);
