@@ -417,6 +417,10 @@ typedef struct {
     int64_t level_nodes[4];      /* factor-tree vertices per level (level A-1: leaves) */
     double block_flops_per_site; /* projected blocks of the used entries, per sink site */
     double tree_flops_per_slice; /* factor-tree evaluation, per time slice */
+    int64_t shared_sums;         /* the factor tree's level-(A-2) vertices hash-consed by their
+                                    leaf sums (Sec. 5's congruence on the block terms): distinct
+                                    sums with equal factor and weight lists (A >= 2, else 0) */
+    int64_t shared_sum_terms;    /* leaf terms of those distinct sums */
 } mbc_block_plan_info;
 mbc_status mbc_block_plan_get_info(const mbc_block_plan* plan, mbc_block_plan_info* info);
 /* Merged terms: ids [merged_terms][A] (type * MBC_BLOCK_ENTRIES + eta, ascending within

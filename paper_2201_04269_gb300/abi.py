@@ -70,7 +70,8 @@ class mbc_block_plan_info(ctypes.Structure):
     _fields_ = [("n_baryons", ctypes.c_int), ("n_products", ctypes.c_int), ("n_w", ctypes.c_int * 8),
                 ("expanded_terms", ctypes.c_int64), ("merged_terms", ctypes.c_int64), ("factors", ctypes.c_int64),
                 ("level_nodes", ctypes.c_int64 * 4), ("block_flops_per_site", ctypes.c_double),
-                ("tree_flops_per_slice", ctypes.c_double)]
+                ("tree_flops_per_slice", ctypes.c_double), ("shared_sums", ctypes.c_int64),
+                ("shared_sum_terms", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -57,6 +57,10 @@ struct BlockHostPlan {
     std::vector<int32_t> unit_leaf;        // [n_units + 1] first leaf of each unit
     std::vector<uint16_t> leaf_f;          // [K] compact factor of each leaf
     int64_t level_nodes[4] = {0, 0, 0, 0};
+    // hash-consing of the units' leaf sums (Sec. 5's congruence step on the block terms):
+    // distinct sums sum_leaves w F[leaf] among the units (equal factor and weight lists),
+    // and the leaf terms of those distinct sums (A >= 2; 0 otherwise)
+    int64_t shared_sums = 0, shared_sum_terms = 0;
     double block_flops_per_site = 0, tree_flops_per_slice = 0;
 };
 std::string plan_blocks(BlockHostPlan& bp);                // blocks_planner.cpp

@@ -253,6 +253,8 @@ mbc_status mbc_block_plan_get_info(const mbc_block_plan* P, mbc_block_plan_info*
     for (int a = 0; a < 4; ++a) info->level_nodes[a] = h.level_nodes[a];
     info->block_flops_per_site = h.block_flops_per_site;
     info->tree_flops_per_slice = h.tree_flops_per_slice;
+    info->shared_sums = h.shared_sums;
+    info->shared_sum_terms = h.shared_sum_terms;
     return MBC_OK;
 }
 

@@ -29,6 +29,8 @@
 
 #include "blocks.hpp"
 
+#include <cstring>
+
 namespace mbc {
 
 namespace {
@@ -227,6 +229,51 @@ std::string plan_blocks(BlockHostPlan& bp) {
     bp.block_flops_per_site = fl + (double)bp.factor.size() * 6 * 8;
     const int64_t n_units = (int64_t)bp.unit_leaf.size() - 1;
     bp.tree_flops_per_slice = 8.0 * ((double)K + (double)n_units * (A - 1));
+    // hash-consed leaf sums: a 64-bit hash per unit (FNV-1a over its leaves' factors and
+    // weight bits), units sorted by hash, equal hashes compared leaf by leaf
+    bp.shared_sums = bp.shared_sum_terms = 0;
+    if (A >= 2 && n_units > 0) {
+        auto leaf_eq = [&](int64_t x, int64_t y) {
+            return bp.leaf_f[x] == bp.leaf_f[y] && bp.w[x] == bp.w[y];
+        };
+        std::vector<std::pair<uint64_t, int64_t>> hu((size_t)n_units);
+        for (int64_t u = 0; u < n_units; ++u) {
+            uint64_t h = 1469598103934665603ull;
+            auto mix = [&](uint64_t v) {
+                for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xFFu; h *= 1099511628211ull; }
+            };
+            for (int32_t l = bp.unit_leaf[u]; l < bp.unit_leaf[u + 1]; ++l) {
+                uint64_t re, im;
+                const double wr = bp.w[l].real(), wi = bp.w[l].imag();
+                std::memcpy(&re, &wr, 8);
+                std::memcpy(&im, &wi, 8);
+                mix(bp.leaf_f[l]);
+                mix(re);
+                mix(im);
+            }
+            hu[(size_t)u] = {h, u};
+        }
+        std::sort(hu.begin(), hu.end());
+        std::vector<int64_t> reps;                   // distinct units among one hash value
+        for (size_t i = 0; i < hu.size(); ++i) {
+            if (i == 0 || hu[i].first != hu[i - 1].first) reps.clear();
+            const int64_t u = hu[i].second;
+            const int32_t a0 = bp.unit_leaf[u], n = bp.unit_leaf[u + 1] - a0;
+            bool found = false;
+            for (int64_t r : reps) {
+                const int32_t b0 = bp.unit_leaf[r];
+                if (bp.unit_leaf[r + 1] - b0 != n) continue;
+                bool same = true;
+                for (int32_t k = 0; k < n && same; ++k) same = leaf_eq(a0 + k, b0 + k);
+                if (same) { found = true; break; }
+            }
+            if (!found) {
+                reps.push_back(u);
+                ++bp.shared_sums;
+                bp.shared_sum_terms += n;
+            }
+        }
+    }
     return "";
 }
 

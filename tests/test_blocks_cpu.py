@@ -79,3 +79,22 @@ def test_block_argument_errors(abi, hctx):
         abi.mbc_block_correlator(p, 1, 1, -1, 1, 2, 1, ctx=hctx)
     assert e.value.status == 1
     abi.mbc_block_plan_destroy(p)
+
+
+@pytest.mark.parametrize("name", ["dinucleon_I", "he3_I"])
+def test_shared_leaf_sums_match_oracle(abi, hctx, name):
+    """The planner's hash-consing of the factor tree's level-(A-2) vertices by their leaf
+    sums (Sec. 5's congruence on the block terms) counts the same distinct sums, and the
+    same leaf terms among them, as a plain grouping of the oracle's merged terms."""
+    ref = obl.BlockPlan(name, "canonical")
+    A = ref.A
+    prefix = ref.ids[:, :A - 1]
+    starts = np.flatnonzero(np.r_[True, np.any(prefix[1:] != prefix[:-1], axis=1)])
+    ends = np.r_[starts[1:], len(ref.W)]
+    sums = {tuple(zip(ref.ids[a:b, A - 1].tolist(), ref.W[a:b].tolist())) for a, b in zip(starts, ends)}
+    plan = abi.mbc_block_plan_create(hctx, name)
+    info = abi.mbc_block_plan_get_info(plan)
+    assert info["level_nodes"][A - 2] == len(starts)
+    assert info["shared_sums"] == len(sums)
+    assert info["shared_sum_terms"] == sum(len(s) for s in sums)
+    abi.mbc_block_plan_destroy(plan)
