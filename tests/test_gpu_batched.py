@@ -167,6 +167,57 @@ def test_batch_mixing_all_three_arithmetics(ctx):
         pl.destroy()
 
 
+def test_fp32_batch_with_complex_weight_item(ctx):
+    """An item with complex weights (and a projector) in an FP32 batch switches the launch to
+    the complex-weight records for every item: the real-weight He-3 I item and the complex
+    item still equal their separate calls, and the complex item matches the oracle's
+    index-set sum."""
+    from paper_2201_04269_gb300 import abi, Plan
+    from oracle import native as onat_
+    n_u, n_d = 3, 2
+    rng = np.random.default_rng(33)
+
+    def side(n):
+        idx = np.zeros((n, n_u + n_d), np.int8)
+        for t in range(n):
+            idx[t, :n_u] = rng.choice(12, n_u, replace=False)
+            idx[t, n_u:] = rng.choice(12, n_d, replace=False)
+        return idx, rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    si, sw = side(20)
+    ri, rw = side(16)
+    soff, roff = np.array([0, 9, 20]), np.array([0, 7, 16])
+    P = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    pc = Plan(ctx, abi.mbc_plan_create(ctx.handle, n_u, n_d, si, sw, soff, ri, rw, roff, P, 1.0, "egraph", "fp32"))
+    pr = ctx.plan_operator("he3_I", "egraph", "fp32")
+    L, T = 3, 2
+    U, D = mi.workload_fields("batched_64", set_index=9, L=L, T=T)
+    Ud, Dd = torch.from_numpy(U[None]).cuda(), torch.from_numpy(D[None]).cuda()
+    items, keep = [], []
+    for pl in (pr, pc):
+        C = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+        S = torch.zeros(1, T, L ** 3, dtype=torch.complex128, device="cuda")
+        keep += [C, S]
+        items.append(dict(plan=pl.handle, U=Ud, D=Dd, C=C, site_out=S, n_sets=1, T=T, V3=L ** 3))
+    ctx.batch(items)
+    torch.cuda.synchronize()
+    for it, pl in zip(items, (pr, pc)):
+        C1 = torch.zeros(1, T, dtype=torch.complex128, device="cuda")
+        S1 = torch.zeros(1, T, L ** 3, dtype=torch.complex128, device="cuda")
+        pl.correlator(Ud, Dd, C1, S1)
+        torch.cuda.synchronize()
+        assert relerr(it["C"].cpu().numpy(), C1.cpu().numpy()) <= 1e-9
+        assert relerr(it["site_out"].cpu().numpy(), S1.cpu().numpy()) <= 1e-9
+    snk = [(si[soff[j]:soff[j + 1]], sw[soff[j]:soff[j + 1]]) for j in range(2)]
+    src = [(ri[roff[j]:roff[j + 1]], rw[roff[j]:roff[j + 1]]) for j in range(2)]
+    n = n_u + n_d
+    ref = (-1) ** (n * (n - 1) // 2) * onat_.direct(n_u, n_d, snk, src, P, U.reshape(-1, 12, 12), D.reshape(-1, 12, 12))
+    assert relerr(items[1]["site_out"].cpu().numpy().ravel(), ref) <= SITE_TOL
+    ref_he3 = oracle_sites("he3_I", U, D)
+    assert relerr(items[0]["site_out"].cpu().numpy().ravel(), ref_he3) <= SITE_TOL
+    pr.destroy()
+    pc.destroy()
+
+
 def test_batched_workload_64_sets_full_size(ctx):
     """The batched workload at its stated size in one persistent FP32 launch (plus its
     guard, recompute and site-sum launches): three sampled sites of every item against
